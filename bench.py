@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Throughput of the exact DBSCAN hot path on GB300; prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+A step is one full clustering (prep, pair test + count -> core flags, union,
+border, labels) of one synthetic instance already resident in HBM.  The
+default workload is n = 500,000 points in d = 2 (50 Gaussian blobs with sigma
+log-uniform in [0.002, 0.02] plus 20% noise, eps = 0.005, min_pts = 10), which
+runs on the eps-grid path.
+
+Metric: G pair-tests/s, where the pair tests of a step are the ordered
+candidate pairs of the instance's eps-grid (every (p, q) with q in a cell of
+p's neighbourhood), a fixed property of the input; the same count is the unit
+of the CPU baseline, so the two are comparable.  The L2 is flushed (a 256 MiB
+write) before every timed step; each step is timed with CUDA events on the
+plan's stream.  With N > 1 (torchrun) every rank runs its own replica on its
+own GPU (the path does not shard) and the value is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1506_02226_gb300 import inputs  # noqa: E402
+
+WORKLOADS = {
+    "lowd2": ("500k points, d=2, 50 blobs + 20% noise, eps=0.005, min_pts=10", lambda: inputs.large_lowd(2)),
+    "lowd3": ("500k points, d=3, 50 blobs + 20% noise, eps=0.005, min_pts=10", lambda: inputs.large_lowd(3)),
+    "small": ("2k points, d=2, 5 blobs + 10% noise, eps=0.02, min_pts=5", inputs.small_2d),
+}
+CPU_SAMPLE = {"lowd2": 200_000, "lowd3": 200_000, "small": 2000}
+
+
+# ------------------------------------------------------------------ work units
+def grid_candidate_pairs(points: np.ndarray, eps: float) -> int:
+    """Ordered candidate pairs of the eps-grid (host-side count, numpy).
+
+    Cell side c = floor(sqrt(floor(T/d))) + 1 grid units; a point's candidates
+    are the points of its own cell and of every cell offset o with
+    sum_k [o_k != 0]((|o_k|-1)c+1)^2 <= T.
+    """
+    u = np.rint(points.astype(np.float64) * 1024).astype(np.int64)
+    n, d = u.shape
+    e = float(np.float32(eps))
+    T = min(math.floor(e * e * 1048576.0), d * 1023 * 1023)
+    c = math.isqrt(T // d) + 1
+    s = math.isqrt(T)
+    r = -(-s // c)
+    G = -(-1024 // c)
+    cells = u // c
+    key = np.zeros(n, np.int64)
+    for k in reversed(range(d)):
+        key = key * G + cells[:, k]
+    uk, cnt = np.unique(key, return_counts=True)
+    coords = np.stack([(uk // G ** k) % G for k in range(d)], axis=1)
+    total = np.zeros(len(uk), np.int64)
+    import itertools
+    for off in itertools.product(range(-r, r + 1), repeat=d):
+        md = sum(((abs(o) - 1) * c + 1) ** 2 for o in off if o)
+        if md > T:
+            continue
+        nc = coords + np.array(off)
+        ok = np.all((nc >= 0) & (nc < G), axis=1)
+        nk = np.zeros(len(uk), np.int64)
+        for k in reversed(range(d)):
+            nk = nk * G + nc[:, k]
+        pos = np.searchsorted(uk, nk)
+        pos = np.clip(pos, 0, len(uk) - 1)
+        hit = ok & (uk[pos] == nk)
+        total += np.where(hit, cnt[pos], 0)
+    return int((cnt * total).sum())
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [l.split(", ") for l in out.strip().splitlines() if l.count(",") >= 8]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ roofline
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return {"hbm_gbs": p["hbm_gbs"], "sm_max_mhz": p.get("sm_max_mhz", 2070.0), "src": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "src": "fallback"}
+
+
+def algorithmic_work(name: str, n: int, d: int, st: dict):
+    """(bound, work per launch, unit) of a kernel: bytes it must move at least,
+    counted from the data it reads and writes once (HBM-bound kernels)."""
+    cells = max(st.get("cells", 0), 1)
+    table = {
+        # x (4d) in; slot (4) + packed point (16) out; one hash read/atomic (8) per point
+        "grid_prep": 4 * d + 4 + 16 + 8,
+        # slot (4), cursor atomic (4), cell id (4), packed point (16) in; point, index, cell (24) out
+        "grid_scatter": 4 + 4 + 4 + 16 + 24,
+        # cell id, index, cell size, packed point in (28); core flag (1) out
+        "grid_count": 28 + 1,
+        # cell id, index, flag, rep in (13); parent (4) out
+        "grid_union_init": 13 + 4,
+        # index, cell, flag (9) in; parent chain (8) + label (4)
+        "grid_label": 9 + 8 + 4,
+    }
+    if name in table:
+        return "hbm", table[name] * n, "GB/s"
+    if name == "grid_cells":
+        return "hbm", 0, "GB/s"
+    if name == "grid_nbrs":
+        return "hbm", 0, "GB/s"
+    return None, 0, None
+
+
+# ------------------------------------------------------------------ arms
+def run_reference(args, wl_name):
+    """The oracle (plain CPU brute force) timed on bounded samples of the workload."""
+    import oracle
+    desc, make = WORKLOADS[wl_name]
+    inst = make()
+    cores = os.cpu_count() or 1
+    # Size the per-step sample so that warm-up + timed steps take about two minutes
+    # (brute force costs ~m^2): calibrate on a small subsample first.
+    m0 = min(20_000, inst.n)
+    cal = inputs.subsample(inst, m0, seed=999)
+    t0 = time.perf_counter()
+    oracle.dbscan(cal.points, cal.eps, cal.min_pts, nthreads=cores)
+    t_cal = max(time.perf_counter() - t0, 1e-3)
+    target = min(10.0, 120.0 / (args.warmup + args.steps))
+    m = int(min(inst.n, max(2000, m0 * math.sqrt(target / t_cal))))
+    times, units = [], []
+    for step in range(args.warmup + args.steps):
+        sub = inputs.subsample(inst, m, seed=step)
+        t0 = time.perf_counter()
+        oracle.dbscan(sub.points, sub.eps, sub.min_pts, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+            units.append(grid_candidate_pairs(sub.points, sub.eps))
+    value = sum(units) / sum(times) / 1e9
+    ms = 1e3 * sum(times) / len(times)
+    sample = f"oracle on {m}-point uniform subsamples of the {desc} workload, one per step"
+    print(json.dumps({
+        "impl": "reference", "metric": "G pair-tests/s", "value": value, "unit": "G pair-tests/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": wl_name + ": " + desc, "sample_points": m},
+        "cpu_baseline": {"value": value, "unit": "G pair-tests/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "G pair-tests/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def cpu_baseline(inst, wl_name, desc):
+    import oracle
+    m = min(CPU_SAMPLE[wl_name], inst.n)
+    sub = inputs.subsample(inst, m, seed=12345)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.dbscan(sub.points, sub.eps, sub.min_pts, nthreads=cores)
+    dt = time.perf_counter() - t0
+    units = grid_candidate_pairs(sub.points, sub.eps)
+    return {"value": units / dt / 1e9, "unit": "G pair-tests/s", "cores": cores, "kind": "oracle",
+            "sample": f"full oracle run on a {m}-point uniform subsample of the {desc} workload "
+                      f"({units} candidate pairs, {dt:.2f} s)"}
+
+
+def run_ours(args, wl_name):
+    import torch
+    from paper_1506_02226_gb300 import binding as B
+    from paper_1506_02226_gb300.api import Plan
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    desc, make = WORKLOADS[wl_name]
+    inst = make()
+    n, d = inst.n, inst.d
+    x = torch.from_numpy(inst.points).cuda()
+    labels = torch.empty(n, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    # one synchronous run for the statistics (and the launch count)
+    with Plan(max_n=n, max_d=d) as p:
+        _, st0 = p.run(x, inst.eps, inst.min_pts, stats=True)
+    units = st0["candidate_pairs"]
+    if st0["path"] == B.DBSCAN_PATH_GRID:
+        host_units = grid_candidate_pairs(inst.points, inst.eps)
+        if host_units != units:
+            raise RuntimeError(f"candidate-pair count mismatch: device {units} host {host_units}")
+
+    plan = Plan(max_n=n, max_d=d, synchronous=False, stream=stream, profile=True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    kern: dict[str, list[float]] = {}
+    step_ms = []
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            plan.run(x, inst.eps, inst.min_pts, labels=labels)
+        if plan.sync() != 0:
+            raise RuntimeError("warm-up run reported an error")
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        time.sleep(0.3)
+        for _ in range(args.steps):
+            flush.fill_(1)  # evict the 129 MB L2 before the timed step
+            ev0.record(stream)
+            plan.run(x, inst.eps, inst.min_pts, labels=labels)
+            ev1.record(stream)
+            ev1.synchronize()
+            step_ms.append(ev0.elapsed_time(ev1))
+            for nm, ms in plan.phase_times():
+                kern.setdefault(nm, []).append(ms)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+    if plan.sync() != 0:
+        raise RuntimeError("timed run reported an error")
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms_per_step = total_ms / args.steps
+    value = world * units / (ms_per_step * 1e-3) / 1e9
+
+    # end to end: host (pinned) buffers through the C ABI, copies inside the timed region
+    host_pts = torch.from_numpy(inst.points).pin_memory()
+    host_lab = torch.empty(n, dtype=torch.int32).pin_memory()
+    eplan = Plan(max_n=n, max_d=d, stream=stream)
+    for _ in range(2):
+        eplan.run_host(host_pts, inst.eps, inst.min_pts, labels=host_lab)
+    e2e_s = []
+    for _ in range(max(3, args.steps // 4)):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        eplan.run_host(host_pts, inst.eps, inst.min_pts, labels=host_lab)
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_ms = 1e3 * statistics.mean(e2e_s)
+    eplan.close()
+    plan.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    avg = {k: statistics.mean(v) for k, v in kern.items()}
+    dom = max(avg, key=avg.get)
+    peaks = load_peaks()
+    bound, work, unit = algorithmic_work(dom, n, d, st0)
+    roof = None
+    if bound == "hbm" and work:
+        ach = work / (avg[dom] * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_src": peaks["src"],
+                "algorithmic_bytes": work, "avg_ms": avg[dom]}
+    else:
+        roof = {"kernel": dom, "bound": bound, "achieved": None, "peak": None, "unit": unit, "frac": None,
+                "traffic": None, "avg_ms": avg[dom]}
+    cpu = cpu_baseline(inst, wl_name, desc)
+    out = {
+        "metric": "G pair-tests/s", "value": value, "unit": "G pair-tests/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl_name + ": " + desc, "n": n, "d": d, "eps": inst.eps, "min_pts": inst.min_pts,
+                   "path": {1: "eps-grid", 2: "all-pairs SIMT", 3: "all-pairs tensor-core"}.get(st0["path"]),
+                   "l2": "flushed by a 256 MiB write before every timed step", "parallelism": f"replicas x{world}"},
+        "pair_tests_per_step": units,
+        "points_per_s": world * n / (ms_per_step * 1e-3),
+        "clusters": st0["n_clusters"], "core": st0["n_core"], "noise": st0["n_noise"],
+        "kernels_ms": {k: round(v, 5) for k, v in sorted(avg.items(), key=lambda kv: -kv[1])},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": units / (e2e_ms * 1e-3) / 1e9, "unit": "G pair-tests/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": 4 * n * d, "d2h_bytes_per_step": 4 * n},
+        "gpu_launches": st0["kernels"] * args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="lowd2")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        if int(os.environ.get("RANK", "0")) != 0:
+            return
+        run_reference(args, args.workload)
+        return
+    run_ours(args, args.workload)
+
+
+if __name__ == "__main__":
+    main()

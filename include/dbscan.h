@@ -1,0 +1,221 @@
+/*
+ * dbscan.h — C ABI of the GB300 (sm_103a) exact DBSCAN library, libdbscan_gb300.so.
+ *
+ * The method is the three data-parallel steps of Wang et al., "Design and
+ * optimization of DBSCAN Algorithm based on CUDA" (Section I's step list,
+ * Section IV):
+ *   1. the eps-neighbourhood test of every candidate pair, with ||p-q||^2
+ *      compared against eps^2 (Section IV-A) — never stored as a distance matrix;
+ *   2. core points (at least MinPts neighbours, the point itself counted;
+ *      Section II, definition 2) fused with the pair test (Section IV-B,
+ *      "calculate distance and construct primitive clusters at the same time");
+ *   3. merging of reachable core points into clusters (Section II, definition 3;
+ *      Section IV-C), here by a lock-free union-find over core-core eps-edges,
+ *      then border assignment and labelling.
+ *
+ * Exactness.  Coordinates must be multiples of 2^-10 in [0, 1).  With
+ * u = 1024 x (integers 0..1023) and T = floor(eps^2 * 2^20) computed in double
+ * from the float eps, q is a neighbour of p iff sum_k (u_pk - u_qk)^2 <= T.
+ * Every kernel decides this predicate exactly, so the labels are a pure
+ * function of the input:
+ *   - a core point's label is the smallest core index of its cluster;
+ *   - a border point (non-core with a core neighbour) takes the label of its
+ *     smallest-index core neighbour;
+ *   - noise is -1;
+ *   - DBSCAN_LABEL_COMPACT renumbers cluster ids to 0..k-1 in increasing order
+ *     of their smallest core index.
+ *
+ * Memory.  Unless a function says otherwise, `points` and `labels_out` are
+ * DEVICE pointers owned by the caller; the library never frees them and keeps
+ * no reference after the call (serve jobs hold theirs until they are done).
+ * Points are row-major float32 n x d.  A plan owns all its workspace (device
+ * memory allocated in dbscan_plan_create).
+ *
+ * Errors.  Every function returns an int status: 0 (DBSCAN_OK) or a
+ * DBSCAN_ERR_* code; dbscan_strerror() names it.  Checks done on the device
+ * (the 2^-10 grid test, bounded waits) are reported when the plan is
+ * synchronous, or by dbscan_plan_sync() otherwise.
+ *
+ * Threads.  A plan is not thread-safe: one host thread at a time.  The serve
+ * API's submit/poll/wait are thread-safe.
+ */
+#ifndef DBSCAN_GB300_H
+#define DBSCAN_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DBSCAN_ABI_VERSION 1
+
+/* Status codes. */
+#define DBSCAN_OK 0
+#define DBSCAN_ERR_ARG 1           /* null pointer, n < 0, d < 1, eps <= 0 or not finite, min_pts < 1, n > max_n, d > max_d */
+#define DBSCAN_ERR_NOT_QUANTISED 2 /* a coordinate is not k * 2^-10 with 0 <= k <= 1023 (checked on the device) */
+#define DBSCAN_ERR_OOM 3           /* device or host allocation failed */
+#define DBSCAN_ERR_CUDA 4          /* a CUDA runtime call failed */
+#define DBSCAN_ERR_TIMEOUT 5       /* a bounded device-side wait or a host wait expired */
+#define DBSCAN_ERR_BUSY 6          /* serve admission is full (slots or HBM budget) */
+#define DBSCAN_ERR_UNSUPPORTED 7   /* option or shape this build does not handle */
+#define DBSCAN_ERR_NOT_FOUND 8     /* unknown serve job id */
+
+/* Pair-test arithmetic. */
+#define DBSCAN_PREC_AUTO 0       /* tensor-core FP16 Gram for d >= 16 all-pairs, SIMT otherwise */
+#define DBSCAN_PREC_EXACT_SIMT 1 /* FP32/INT32 CUDA-core pair test, exact by construction */
+#define DBSCAN_PREC_FP16_GRAM 2  /* tcgen05 FP16 Gram product + exact recheck of the rounding band */
+#define DBSCAN_PREC_BF16_GRAM 3  /* tcgen05 BF16 Gram product + exact recheck of the rounding band */
+
+/* Candidate generation. */
+#define DBSCAN_GRID_AUTO 0 /* eps-grid for d <= 3, all pairs otherwise */
+#define DBSCAN_GRID_ON 1   /* eps-grid (d <= 3 only; else DBSCAN_ERR_UNSUPPORTED) */
+#define DBSCAN_GRID_OFF 2  /* all pairs */
+
+/* Label numbering. */
+#define DBSCAN_LABEL_ROOT_INDEX 0 /* cluster id = smallest core index in the cluster */
+#define DBSCAN_LABEL_COMPACT 1    /* cluster ids 0..k-1 in increasing order of that index */
+
+/* Which path a run took (dbscan_stats.path). */
+#define DBSCAN_PATH_NONE 0
+#define DBSCAN_PATH_GRID 1
+#define DBSCAN_PATH_ALLPAIRS_SIMT 2
+#define DBSCAN_PATH_ALLPAIRS_TC 3
+
+typedef struct dbscan_plan dbscan_plan;
+
+typedef struct dbscan_opts {
+    int32_t device;      /* CUDA device ordinal */
+    int32_t synchronous; /* 1: dbscan_run waits for the device and reports its errors; 0: enqueue only */
+    void *stream;        /* cudaStream_t to enqueue on; NULL = the legacy default stream */
+    int64_t max_n;       /* largest n this plan accepts (workspace is sized for it) */
+    int32_t max_d;       /* largest d this plan accepts */
+    int32_t precision;   /* DBSCAN_PREC_* */
+    int32_t grid;        /* DBSCAN_GRID_* */
+    int32_t label_mode;  /* DBSCAN_LABEL_* */
+    int32_t profile;     /* 1: record a CUDA event after every kernel (see dbscan_plan_phase_times) */
+    int32_t reserved[7]; /* zero */
+} dbscan_opts;
+
+typedef struct dbscan_stats {
+    int64_t n_clusters;      /* clusters found */
+    int64_t n_core;          /* core points */
+    int64_t n_border;        /* border points */
+    int64_t n_noise;         /* noise points */
+    int64_t candidate_pairs; /* ordered pairs the method must decide: n^2 (all pairs) or the pairs
+                                inside each cell's eps-grid neighbourhood (grid path) */
+    int64_t band_pairs;      /* tensor-core path: pairs inside the rounding band, rechecked exactly */
+    int32_t path;            /* DBSCAN_PATH_* */
+    int32_t cells;           /* grid path: occupied cells */
+    int64_t threshold;       /* T = floor(eps^2 * 2^20) */
+    float ms_total;          /* device time of the run (CUDA events), when measured */
+    int32_t kernels;         /* kernel launches the run enqueued */
+    float reserved_f[6];
+} dbscan_stats;
+
+/* Fills *opts with defaults: device 0, synchronous, default stream, max_n 1<<20,
+ * max_d 64, PREC_AUTO, GRID_AUTO, LABEL_ROOT_INDEX. */
+void dbscan_opts_default(dbscan_opts *opts);
+
+/* Creates a plan and allocates its device workspace for (max_n, max_d).
+ * *out receives the plan; on error *out is NULL.  DBSCAN_ERR_OOM if the
+ * workspace does not fit. */
+int dbscan_plan_create(dbscan_plan **out, const dbscan_opts *opts);
+
+/* Waits for the plan's stream, frees its workspace and the plan.  NULL is a no-op. */
+int dbscan_plan_destroy(dbscan_plan *plan);
+
+/* Clusters one point set (Section I's three steps; Section IV).
+ *   points     device, row-major float32 [n][d], on the 2^-10 grid in [0,1)
+ *   n, d       0 <= n <= max_n, 1 <= d <= max_d; n = 0 is a no-op
+ *   eps        finite, > 0 (float32); min_pts >= 1
+ *   labels_out device int32 [n]
+ *   stats      host, nullable; when given, the call synchronises and fills it
+ * Enqueued on the plan's stream.  Synchronous plans return device-side errors
+ * (DBSCAN_ERR_NOT_QUANTISED); asynchronous plans report them from
+ * dbscan_plan_sync().  On an error labels_out is unspecified. */
+int dbscan_run(dbscan_plan *plan, const float *points, int64_t n, int32_t d, float eps, int32_t min_pts,
+               int32_t *labels_out, dbscan_stats *stats);
+
+/* dbscan_run plus per-point diagnostics, both device pointers and nullable:
+ *   counts_out int32 [n]: |eps-neighbourhood| with the point itself (Section II,
+ *              definition 1).  Asking for it turns off the early exit at min_pts.
+ *   core_out   uint8 [n]: 1 for core points (count >= min_pts). */
+int dbscan_run_detail(dbscan_plan *plan, const float *points, int64_t n, int32_t d, float eps,
+                      int32_t min_pts, int32_t *labels_out, int32_t *counts_out, uint8_t *core_out,
+                      dbscan_stats *stats);
+
+/* dbscan_run with HOST buffers: copies points host->device into plan
+ * workspace, clusters, copies labels device->host and waits.  Pinned host
+ * memory gives the fastest copies; pageable memory works.  This is the
+ * end-to-end call. */
+int dbscan_run_host(dbscan_plan *plan, const float *host_points, int64_t n, int32_t d, float eps,
+                    int32_t min_pts, int32_t *host_labels, dbscan_stats *stats);
+
+/* Waits for everything enqueued on the plan and returns the first device-side
+ * error recorded since the last sync (then clears it). */
+int dbscan_plan_sync(dbscan_plan *plan);
+
+/* Per-kernel device times of the plan's last run, measured with CUDA events
+ * on the plan's stream (opts.profile must be 1).  Waits for the run.  Writes
+ * up to max_phases entries: ms[i] is the time of kernel i, names[i] a static
+ * string naming it (nullable arrays); *count receives the number of kernels. */
+int dbscan_plan_phase_times(dbscan_plan *plan, int32_t max_phases, float *ms, const char **names, int32_t *count);
+
+/* Device bytes the plan's workspace holds. */
+int64_t dbscan_plan_workspace_bytes(const dbscan_plan *plan);
+
+/* ---- Batched form: many independent instances in one graph-captured launch sequence ---- */
+
+typedef struct dbscan_instance {
+    const float *points; /* device, row-major float32 [n][d] */
+    int64_t n;
+    int32_t d;
+    float eps;
+    int32_t min_pts;
+    int32_t *labels_out; /* device int32 [n]; labels are local indices 0..n-1 of this instance */
+} dbscan_instance;
+
+/* Clusters `count` independent instances (each as dbscan_run would, with the
+ * plan's label mode; all-pairs SIMT arithmetic).  Uses its own device
+ * workspace, grown on demand and kept by the plan.  Synchronous; per_inst
+ * (host, nullable, `count` entries) receives per-instance counts. */
+int dbscan_batch(dbscan_plan *plan, const dbscan_instance *inst, int32_t count, dbscan_stats *per_inst);
+
+/* ---- Served form: continuous batching of submitted jobs under an HBM budget ---- */
+
+typedef struct dbscan_server dbscan_server;
+
+typedef struct dbscan_serve_opts {
+    int32_t device;
+    int32_t slots;            /* jobs that may be on the device at once */
+    int64_t hbm_budget_bytes; /* admission cap on the summed workspace of in-flight jobs */
+    int32_t label_mode;       /* DBSCAN_LABEL_* */
+    int32_t precision;        /* DBSCAN_PREC_* */
+    int32_t reserved[8];
+} dbscan_serve_opts;
+
+void dbscan_serve_opts_default(dbscan_serve_opts *opts);
+int dbscan_serve_create(dbscan_server **out, const dbscan_serve_opts *opts);
+/* Queues a job; the instance's device buffers must stay valid until it is
+ * done.  *job_id receives its id.  Thread-safe. */
+int dbscan_serve_submit(dbscan_server *srv, const dbscan_instance *inst, uint64_t *job_id);
+/* *done = 1 once the job's labels are written; its status is returned then. */
+int dbscan_serve_poll(dbscan_server *srv, uint64_t job_id, int32_t *done);
+/* Waits up to timeout_us (< 0: forever) for the job.  DBSCAN_ERR_TIMEOUT if it
+ * is not done by then.  latency_us (nullable) receives submit-to-done time. */
+int dbscan_serve_wait(dbscan_server *srv, uint64_t job_id, int64_t timeout_us, double *latency_us);
+int dbscan_serve_destroy(dbscan_server *srv);
+
+/* Static description of a status code. */
+const char *dbscan_strerror(int status);
+
+/* DBSCAN_ABI_VERSION of the loaded library. */
+int32_t dbscan_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DBSCAN_GB300_H */

@@ -1,0 +1,460 @@
+// grid.cu — eps-grid candidate path for d <= 3.
+//
+// The paper tests every pair (Section IV-A).  For d <= 3 this path tests only
+// pairs in nearby grid cells, and decides each with the same exact predicate
+// D(p,q) <= T, so it gives the same labels.
+//
+// Geometry (all in integer grid units):
+//   m = floor(sqrt(floor(T/d))), cell side c = m + 1.  Two points in one cell
+//   differ by at most m per axis, so D <= d*m^2 <= T: every cell is a clique of
+//   mutual eps-neighbours.
+//   s = floor(sqrt(T)) bounds |u_pk - u_qk| for a neighbour, so neighbours lie
+//   within r = ceil(s/c) <= 2 cells per axis; an offset o is kept when its two
+//   cells can hold a pair with D <= T: sum_k [o_k != 0] ((|o_k|-1) c + 1)^2 <= T.
+//
+// Cells are found through an open-addressing hash of the cell key, so no sort
+// is needed: points are counted per cell, each occupied cell reserves a
+// contiguous range, and points are scattered into their cell's range.
+//
+// Steps on the device, each a kernel:
+//   prep     grid check, cell key, hash insert, per-cell count
+//   cells    occupied slot -> cell id and point range (block-aggregated)
+//   scatter  points grouped by cell
+//   nbrs     neighbour-cell table (cell x offset -> cell id or -1)
+//   count    neighbour counts -> core flags (Section IV-B).  A cell with at
+//            least min_pts points makes all its points core with no test; other
+//            points stop counting once they reach min_pts unless exact counts
+//            are requested.  Each cell records its smallest core index (rep).
+//   uinit    each core point hangs under its cell's rep (cells are cliques)
+//   union    neighbouring cells whose cores contain one eps-pair are united
+//            (Section IV-C's merge); a cell pair already in one set is skipped
+//   label    border points take their smallest-index core neighbour; labels
+#include <algorithm>
+#include <climits>
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned hash_slot(unsigned key, int bits) { return (key * 2654435761u) >> (32 - bits); }
+
+__device__ __forceinline__ unsigned cell_key_of(const int *u, const GridGeom &g) {
+    unsigned cx = (unsigned)(u[0] / g.c);
+    unsigned cy = g.d > 1 ? (unsigned)(u[1] / g.c) : 0u;
+    unsigned cz = g.d > 2 ? (unsigned)(u[2] / g.c) : 0u;
+    return (cz * (unsigned)g.G + cy) * (unsigned)g.G + cx;
+}
+
+__global__ void grid_prep_kernel(const float *__restrict__ x, int n, GridGeom g, unsigned *hkey, int *hcount,
+                                 int *__restrict__ slot_of, float4 *__restrict__ pts4, unsigned *status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool valid = i < n;
+    int slot = -1 - lane;
+    if (valid) {
+        int u[3] = {0, 0, 0};
+        bool ok = true;
+        for (int k = 0; k < g.d; ++k) {
+            int uk;
+            ok &= db::on_grid(x[(size_t)i * g.d + k], uk);
+            u[k] = uk;
+        }
+        if (!ok) atomicOr(status, DB_EBIT_NOT_QUANTISED);
+        const unsigned key = cell_key_of(u, g);
+        const unsigned mask = (1u << g.hbits) - 1u;
+        unsigned h = hash_slot(key, g.hbits);
+        bool placed = false;
+        for (unsigned probe = 0; probe <= mask; ++probe) {
+            unsigned cur = ld_relaxed_u32(hkey + h);
+            if (cur == key) { placed = true; break; }
+            if (cur == DB_HASH_EMPTY) {
+                unsigned prev = atomicCAS(hkey + h, DB_HASH_EMPTY, key);
+                if (prev == DB_HASH_EMPTY || prev == key) { placed = true; break; }
+            }
+            h = (h + 1) & mask;
+        }
+        if (!placed) {  // cannot happen with >= 2n slots; keep memory safe if it does
+            atomicOr(status, DB_EBIT_OVERFLOW);
+            h = 0;
+        }
+        slot = (int)h;
+        slot_of[i] = slot;
+        const float f0 = (float)u[0], f1 = (float)u[1], f2 = (float)u[2];
+        pts4[i] = make_float4(f0, f1, f2, -(f0 * f0 + f1 * f1 + f2 * f2));
+    }
+    // One atomic per distinct cell in the warp.
+    const unsigned peers = __match_any_sync(0xffffffffu, slot);
+    if (valid && lane == __ffs(peers) - 1) atomicAdd(hcount + slot, __popc(peers));
+}
+
+constexpr int CELLS_PER_THREAD = 4;
+
+__global__ void grid_cells_kernel(int H, const unsigned *__restrict__ hkey, const int *__restrict__ hcount,
+                                  int *__restrict__ hval, int *__restrict__ hcursor, int *__restrict__ cell_start,
+                                  int *__restrict__ cell_count, unsigned *__restrict__ cell_key,
+                                  int *__restrict__ cell_rep, unsigned long long *ctr0) {
+    __shared__ int wocc[32], wcnt[32];
+    __shared__ unsigned long long base;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int s0 = (blockIdx.x * blockDim.x + threadIdx.x) * CELLS_PER_THREAD;
+    int cnt[CELLS_PER_THREAD];
+    int tocc = 0, tcnt = 0;
+#pragma unroll
+    for (int k = 0; k < CELLS_PER_THREAD; ++k) {
+        cnt[k] = (s0 + k < H) ? hcount[s0 + k] : 0;
+        tocc += cnt[k] > 0;
+        tcnt += cnt[k];
+    }
+    int xo = tocc, xc = tcnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        int yo = __shfl_up_sync(0xffffffffu, xo, o), yc = __shfl_up_sync(0xffffffffu, xc, o);
+        if (lane >= o) { xo += yo; xc += yc; }
+    }
+    if (lane == 31) { wocc[wid] = xo; wcnt[wid] = xc; }
+    __syncthreads();
+    int offo = 0, offc = 0, toto = 0, totc = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        if (w < wid) { offo += wocc[w]; offc += wcnt[w]; }
+        toto += wocc[w];
+        totc += wcnt[w];
+    }
+    if (threadIdx.x == 0)
+        base = (toto || totc) ? atomicAdd(ctr0, ((unsigned long long)toto << 32) | (unsigned)totc) : 0ull;
+    __syncthreads();
+    int cid = (int)(base >> 32) + offo + xo - tocc;
+    int start = (int)(base & 0xffffffffull) + offc + xc - tcnt;
+#pragma unroll
+    for (int k = 0; k < CELLS_PER_THREAD; ++k) {
+        if (cnt[k] > 0) {
+            const int s = s0 + k;
+            cell_start[cid] = start;
+            cell_count[cid] = cnt[k];
+            cell_key[cid] = hkey[s];
+            cell_rep[cid] = DB_NONE;
+            hval[s] = cid;
+            hcursor[s] = start;
+            ++cid;
+            start += cnt[k];
+        }
+    }
+}
+
+__global__ void grid_scatter_kernel(int n, const int *__restrict__ slot_of, int *hcursor, const int *__restrict__ hval,
+                                    const float4 *__restrict__ pts4, float4 *__restrict__ spts, int *__restrict__ sidx,
+                                    int *__restrict__ scell) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool valid = i < n;
+    const int slot = valid ? slot_of[i] : -1 - lane;
+    const unsigned peers = __match_any_sync(0xffffffffu, slot);
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (valid && lane == leader) base = atomicAdd(hcursor + slot, __popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (!valid) return;
+    const int pos = base + __popc(peers & db::lanemask_lt());
+    spts[pos] = pts4[i];
+    sidx[pos] = i;
+    scell[pos] = hval[slot];
+}
+
+__global__ void grid_nbr_kernel(GridGeom g, const unsigned long long *ctr0, const unsigned *__restrict__ cell_key,
+                                const unsigned *__restrict__ hkey, const int *__restrict__ hval, int *__restrict__ nbr) {
+    const int ncells = (int)(*ctr0 >> 32);
+    const int64_t total = (int64_t)ncells * g.noff;
+    const unsigned mask = (1u << g.hbits) - 1u;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int A = (int)(t / g.noff), o = (int)(t - (int64_t)A * g.noff);
+        const unsigned key = cell_key[A];
+        const int G = g.G;
+        const int c[3] = {(int)(key % G), (int)((key / G) % G), (int)(key / ((unsigned)G * G))};
+        const char4 off = g.off[o];
+        const int nc[3] = {c[0] + off.x, c[1] + off.y, c[2] + off.z};
+        int res = -1;
+        if (nc[0] >= 0 && nc[0] < G && nc[1] >= 0 && nc[1] < G && nc[2] >= 0 && nc[2] < G) {
+            const unsigned k2 = ((unsigned)nc[2] * G + (unsigned)nc[1]) * G + (unsigned)nc[0];
+            unsigned h = hash_slot(k2, g.hbits);
+            for (unsigned probe = 0; probe <= mask; ++probe) {
+                unsigned cur = hkey[h];
+                if (cur == k2) { res = hval[h]; break; }
+                if (cur == DB_HASH_EMPTY) break;
+                h = (h + 1) & mask;
+            }
+        }
+        nbr[t] = res;
+    }
+}
+
+// Exact score T + 1 - D(p,q) in the Gram form of Section IV-B: every partial
+// sum is an integer below 2*3*1023^2 < 2^24 in magnitude, so FP32 is exact.
+template <int D>
+__device__ __forceinline__ bool is_nbr(float cp, float px2, float py2, float pz2, float4 q) {
+    float acc = cp + q.w;
+    acc = fmaf(px2, q.x, acc);
+    if (D > 1) acc = fmaf(py2, q.y, acc);
+    if (D > 2) acc = fmaf(pz2, q.z, acc);
+    return acc >= 1.f;
+}
+
+template <int D>
+__global__ void grid_count_kernel(int n, GridGeom g, const float4 *__restrict__ spts, const int *__restrict__ sidx,
+                                  const int *__restrict__ scell, const int *__restrict__ cell_start,
+                                  const int *__restrict__ cell_count, const int *__restrict__ nbr, int min_pts,
+                                  int exact, uint8_t *__restrict__ score, int *cell_rep, int *__restrict__ counts_out,
+                                  uint8_t *__restrict__ core_out) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = p < n;
+    bool core = false;
+    int A = -1, orig = DB_NONE;
+    if (valid) {
+        A = scell[p];
+        orig = sidx[p];
+        int cnt = cell_count[A];  // the own cell is a clique: all of it is in the neighbourhood
+        if (exact || cnt < min_pts) {
+            const float4 pt = spts[p];
+            const float cp = g.Tp1 + pt.w, px2 = 2.f * pt.x, py2 = 2.f * pt.y, pz2 = 2.f * pt.z;
+            const int *row = nbr + (size_t)A * g.noff;
+            const int lim = exact ? INT_MAX : min_pts;  // early exit at min_pts (Section II def. 2)
+            for (int o = 0; o < g.noff && cnt < lim; ++o) {
+                const int B = row[o];
+                if (B < 0) continue;
+                const int s = cell_start[B], e = s + cell_count[B];
+                for (int q = s; q < e && cnt < lim; ++q) cnt += is_nbr<D>(cp, px2, py2, pz2, spts[q]);
+            }
+        }
+        core = cnt >= min_pts;
+        score[p] = core;
+        if (counts_out) counts_out[orig] = cnt;
+        if (core_out) core_out[orig] = core;
+    }
+    // Smallest core index per cell, one atomic per (warp, cell).
+    const unsigned cmask = __ballot_sync(0xffffffffu, core);
+    if (core) {
+        const unsigned peers = __match_any_sync(cmask, A);
+        const int m = (int)__reduce_min_sync(peers, (unsigned)orig);
+        if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicMin(cell_rep + A, m);
+    }
+}
+
+__global__ void grid_union_init_kernel(int n, const int *__restrict__ sidx, const int *__restrict__ scell,
+                                       const uint8_t *__restrict__ score, const int *__restrict__ cell_rep,
+                                       int *__restrict__ parent) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const int orig = sidx[p];
+        parent[orig] = score[p] ? cell_rep[scell[p]] : orig;
+    }
+}
+
+template <int D>
+__global__ void grid_union_kernel(int n, GridGeom g, const float4 *__restrict__ spts, const int *__restrict__ scell,
+                                  const uint8_t *__restrict__ score, const int *__restrict__ cell_start,
+                                  const int *__restrict__ cell_count, const unsigned *__restrict__ cell_key,
+                                  const int *__restrict__ cell_rep, const int *__restrict__ nbr, int *parent,
+                                  unsigned *status) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n || !score[p]) return;
+    const int A = scell[p];
+    const unsigned keyA = cell_key[A];
+    const int repA = cell_rep[A];
+    const float4 pt = spts[p];
+    const float cp = g.Tp1 + pt.w, px2 = 2.f * pt.x, py2 = 2.f * pt.y, pz2 = 2.f * pt.z;
+    const int *row = nbr + (size_t)A * g.noff;
+    for (int o = 0; o < g.noff; ++o) {
+        const int B = row[o];
+        if (B < 0 || cell_key[B] < keyA) continue;  // each cell pair from its smaller key
+        const int repB = cell_rep[B];
+        if (repB == DB_NONE) continue;
+        if (db::uf_find(parent, repA) == db::uf_find(parent, repB)) continue;
+        const int s = cell_start[B], e = s + cell_count[B];
+        for (int q = s; q < e; ++q) {
+            if (score[q] && is_nbr<D>(cp, px2, py2, pz2, spts[q])) {
+                db::uf_unite(parent, repA, repB, status);
+                break;
+            }
+        }
+    }
+}
+
+template <int D>
+__global__ void grid_label_kernel(int n, GridGeom g, const float4 *__restrict__ spts, const int *__restrict__ sidx,
+                                  const int *__restrict__ scell, const uint8_t *__restrict__ score,
+                                  const int *__restrict__ cell_start, const int *__restrict__ cell_count,
+                                  const int *__restrict__ cell_rep, const int *__restrict__ nbr, int *parent,
+                                  int *__restrict__ labels, unsigned long long *ctr) {
+    __shared__ int red[4][32];
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    int nc = 0, nb = 0, nn = 0, nr = 0;
+    if (p < n) {
+        const int orig = sidx[p];
+        const int A = scell[p];
+        int lab;
+        if (score[p]) {
+            lab = db::uf_find(parent, orig);
+            nc = 1;
+            nr = lab == orig;
+        } else {
+            int b = cell_rep[A];  // own-cell cores are all neighbours; the rep is the smallest
+            const float4 pt = spts[p];
+            const float cp = g.Tp1 + pt.w, px2 = 2.f * pt.x, py2 = 2.f * pt.y, pz2 = 2.f * pt.z;
+            const int *row = nbr + (size_t)A * g.noff;
+            for (int o = 0; o < g.noff; ++o) {
+                const int B = row[o];
+                if (B < 0 || cell_rep[B] >= b) continue;  // cannot beat b
+                const int s = cell_start[B], e = s + cell_count[B];
+                for (int q = s; q < e; ++q) {
+                    if (!score[q]) continue;
+                    const int qi = sidx[q];
+                    if (qi < b && is_nbr<D>(cp, px2, py2, pz2, spts[q])) b = qi;
+                }
+            }
+            if (b == DB_NONE) {
+                lab = -1;
+                nn = 1;
+            } else {
+                lab = db::uf_find(parent, b);
+                nb = 1;
+            }
+        }
+        labels[orig] = lab;
+    }
+    // block-reduced statistics
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int v[4] = {nc, nb, nn, nr};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+        if (lane == 0) red[k][wid] = v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        int t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[threadIdx.x][w];
+        if (t) atomicAdd(ctr + 2 + threadIdx.x, (unsigned long long)t);
+    }
+}
+
+__global__ void grid_candidates_kernel(GridGeom g, const unsigned long long *ctr0, const int *__restrict__ cell_count,
+                                       const int *__restrict__ nbr, unsigned long long *out) {
+    __shared__ unsigned long long red[32];
+    const int ncells = (int)(*ctr0 >> 32);
+    unsigned long long s = 0;
+    for (int A = blockIdx.x * blockDim.x + threadIdx.x; A < ncells; A += gridDim.x * blockDim.x) {
+        const long long ca = cell_count[A];
+        long long t = ca;
+        for (int o = 0; o < g.noff; ++o) {
+            const int B = nbr[(size_t)A * g.noff + o];
+            if (B >= 0) t += cell_count[B];
+        }
+        s += (unsigned long long)(ca * t);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        if (t) atomicAdd(out, t);
+    }
+}
+
+int64_t isqrt64(int64_t v) {
+    if (v <= 0) return 0;
+    int64_t r = (int64_t)std::sqrt((double)v);
+    while (r * r > v) --r;
+    while ((r + 1) * (r + 1) <= v) ++r;
+    return r;
+}
+
+template <int D>
+cudaError_t grid_pair_passes(const DbWork &w, const GridGeom &g, int n, int min_pts, bool exact, int32_t *labels,
+                             int32_t *counts_out, uint8_t *core_out, cudaStream_t st) {
+    const int nb = (n + 255) / 256;
+    grid_count_kernel<D><<<nb, 256, 0, st>>>(n, g, w.spts, w.sidx, w.scell, w.cell_start, w.cell_count, w.nbr,
+                                             min_pts, exact ? 1 : 0, w.score, w.cell_rep, counts_out, core_out);
+    w.marks->kernel("grid_count", st);
+    grid_union_init_kernel<<<nb, 256, 0, st>>>(n, w.sidx, w.scell, w.score, w.cell_rep, w.parent);
+    w.marks->kernel("grid_union_init", st);
+    grid_union_kernel<D><<<nb, 256, 0, st>>>(n, g, w.spts, w.scell, w.score, w.cell_start, w.cell_count,
+                                             w.cell_key, w.cell_rep, w.nbr, w.parent, w.status);
+    w.marks->kernel("grid_union", st);
+    grid_label_kernel<D><<<nb, 256, 0, st>>>(n, g, w.spts, w.sidx, w.scell, w.score, w.cell_start, w.cell_count,
+                                             w.cell_rep, w.nbr, w.parent, labels, w.ctr);
+    w.marks->kernel("grid_label", st);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool grid_geometry(int32_t d, int64_t Tc, int64_t n, GridGeom *g) {
+    if (d < 1 || d > 3) return false;
+    const int64_t m = isqrt64(Tc / d);
+    const int64_t c = m + 1;
+    const int64_t s = isqrt64(Tc);
+    const int64_t r = (s + c - 1) / c;
+    if (r > 2) return false;  // cannot happen for d <= 3 (s < sqrt(3) c)
+    g->d = d;
+    g->c = (int32_t)c;
+    g->G = (int32_t)((1024 + c - 1) / c);
+    g->Tc = (int32_t)Tc;
+    g->Tp1 = (float)(Tc + 1);
+    int bits = 10;
+    while ((int64_t(1) << bits) < 2 * n) ++bits;
+    g->hbits = bits;
+    int k = 0;
+    const int rz = d > 2 ? (int)r : 0, ry = d > 1 ? (int)r : 0, rx = (int)r;
+    for (int oz = -rz; oz <= rz; ++oz)
+        for (int oy = -ry; oy <= ry; ++oy)
+            for (int ox = -rx; ox <= rx; ++ox) {
+                if (!ox && !oy && !oz) continue;
+                int64_t md = 0;
+                for (int o : {ox, oy, oz})
+                    if (o) {
+                        int64_t gap = (int64_t)(std::abs(o) - 1) * c + 1;
+                        md += gap * gap;
+                    }
+                if (md > Tc) continue;
+                g->off[k++] = make_char4((signed char)ox, (signed char)oy, (signed char)oz, 0);
+            }
+    g->noff = k;
+    return true;
+}
+
+cudaError_t launch_grid_path(const DbWork &w, const GridGeom &g, const float *x, int64_t n64, int32_t min_pts,
+                             bool exact, int32_t *labels, int32_t *counts_out, uint8_t *core_out, cudaStream_t st) {
+    const int n = (int)n64;
+    const int64_t H = int64_t(1) << g.hbits;
+    if (H > w.hcap || g.noff > w.noff_cap) return cudaErrorInvalidValue;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(w.hkey, 0xff, sizeof(unsigned) * H, st))) return e;
+    if ((e = cudaMemsetAsync(w.hcount, 0, sizeof(int) * H, st))) return e;
+    const int nb = (n + 255) / 256;
+    grid_prep_kernel<<<nb, 256, 0, st>>>(x, n, g, w.hkey, w.hcount, w.slot_of, w.pts4, w.status);
+    w.marks->kernel("grid_prep", st);
+    const int cells_per_block = 256 * CELLS_PER_THREAD;
+    grid_cells_kernel<<<(unsigned)((H + cells_per_block - 1) / cells_per_block), 256, 0, st>>>(
+        (int)H, w.hkey, w.hcount, w.hval, w.hcursor, w.cell_start, w.cell_count, w.cell_key, w.cell_rep, w.ctr);
+    w.marks->kernel("grid_cells", st);
+    grid_scatter_kernel<<<nb, 256, 0, st>>>(n, w.slot_of, w.hcursor, w.hval, w.pts4, w.spts, w.sidx, w.scell);
+    w.marks->kernel("grid_scatter", st);
+    grid_nbr_kernel<<<152 * 8, 256, 0, st>>>(g, w.ctr, w.cell_key, w.hkey, w.hval, w.nbr);
+    w.marks->kernel("grid_nbrs", st);
+    if ((e = cudaGetLastError())) return e;
+    switch (g.d) {
+        case 1: return grid_pair_passes<1>(w, g, n, min_pts, exact, labels, counts_out, core_out, st);
+        case 2: return grid_pair_passes<2>(w, g, n, min_pts, exact, labels, counts_out, core_out, st);
+        default: return grid_pair_passes<3>(w, g, n, min_pts, exact, labels, counts_out, core_out, st);
+    }
+}
+
+cudaError_t launch_grid_candidates(const DbWork &w, const GridGeom &g, int64_t /*n*/, cudaStream_t st) {
+    grid_candidates_kernel<<<152 * 4, 256, 0, st>>>(g, w.ctr, w.cell_count, w.nbr, w.ctr + 1);
+    w.marks->kernel("grid_candidates", st);
+    return cudaGetLastError();
+}

@@ -1,0 +1,179 @@
+// internal.cuh — shared device helpers and launch declarations of libdbscan_gb300.
+//
+// Notation follows the paper (Wang et al., Sections II and IV): a point p has
+// grid units u_p (integers 0..1023), T = floor(eps^2 * 2^20) and q is an
+// eps-neighbour of p iff D(p,q) = sum_k (u_pk - u_qk)^2 <= T.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dbscan.h"
+
+// Device-side error bits, OR-ed into the plan's status word.
+#define DB_EBIT_NOT_QUANTISED 1u
+#define DB_EBIT_TIMEOUT 2u     // a bounded loop gave up
+#define DB_EBIT_OVERFLOW 4u    // a device-side list ran out of room
+
+#define DB_NONE 0x7fffffff     // "no index" (larger than every point index)
+#define DB_HASH_EMPTY 0xffffffffu
+
+namespace db {
+
+// ---------------------------------------------------------------------------
+// Relaxed, L1-bypassing accesses for data other threads update concurrently.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int ld_relaxed(const int *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(int *p, int v) {
+    asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Lock-free union-find over point indices (replaces the paper's per-target
+// merge kernel of Section IV-C).  Invariant: parent[x] <= x, and a root is the
+// smallest index of its set, because union always links the larger root under
+// the smaller one.  Path halving writes only ancestors, so concurrent halving
+// and linking keep the invariant.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int uf_find(int *parent, int x) {
+    while (true) {
+        int p = ld_relaxed(parent + x);
+        if (p == x) return x;
+        int gp = ld_relaxed(parent + p);
+        if (gp == p) return p;
+        st_relaxed(parent + x, gp);
+        x = gp;
+    }
+}
+
+// Union of the sets of a and b.  Each failed CAS means another thread linked
+// the root first, so the loop makes global progress; the cap only guards
+// against a corrupted forest and reports it.
+__device__ __forceinline__ void uf_unite(int *parent, int a, int b, unsigned *status) {
+    for (int it = 0; it < (1 << 24); ++it) {
+        a = uf_find(parent, a);
+        b = uf_find(parent, b);
+        if (a == b) return;
+        if (a > b) {
+            int t = a;
+            a = b;
+            b = t;
+        }
+        if (atomicCAS(parent + b, b, a) == b) return;
+    }
+    atomicOr(status, DB_EBIT_TIMEOUT);
+}
+
+// 2^-10 grid check of one coordinate: finite, 0 <= x < 1, 1024 x integral.
+__device__ __forceinline__ bool on_grid(float x, int &u) {
+    float s = x * 1024.0f;  // exact: scaling by a power of two
+    bool ok = (x >= 0.0f) && (x < 1.0f) && (s == floorf(s));
+    u = ok ? (int)s : 0;
+    return ok;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+}  // namespace db
+
+// ---------------------------------------------------------------------------
+// Per-kernel timing: when on, a CUDA event is recorded on the launch stream
+// after every kernel, so kernel i took elapsed(ev[i-1] or start, ev[i]).
+// ---------------------------------------------------------------------------
+struct PhaseMarks {
+    static constexpr int kMax = 32;
+    bool on = false;
+    int n = 0;
+    int kernels = 0;
+    cudaEvent_t start = nullptr;
+    cudaEvent_t ev[kMax] = {};
+    const char *name[kMax] = {};
+    void begin(cudaStream_t st) {
+        n = 0;
+        kernels = 0;
+        if (on) cudaEventRecord(start, st);
+    }
+    void kernel(const char *nm, cudaStream_t st) {
+        ++kernels;
+        if (on && n < kMax) {
+            cudaEventRecord(ev[n], st);
+            name[n++] = nm;
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Workspace of one clustering run (device pointers carved from one allocation).
+// ---------------------------------------------------------------------------
+struct DbWork {
+    int64_t cap_n;
+    int32_t cap_d;
+    int32_t dp_cap;         // padded row stride capacity of P
+    // all paths
+    float *P;               // packed grid units, row stride DP (all-pairs) [cap_n * dp_cap]
+    int32_t *count;         // neighbour counts by point index [cap_n]
+    uint8_t *core;          // core flags by point index [cap_n]
+    int32_t *parent;        // union-find forest by point index [cap_n]
+    int32_t *border;        // smallest core neighbour of non-core points [cap_n]
+    int32_t *scan;          // exclusive-scan output [cap_n + 1]
+    int32_t *scan_part;     // scan partials
+    int64_t scan_part_cap;
+    unsigned *status;       // device error bits
+    unsigned long long *ctr;  // counters: [0]=cells|points, [1]=candidate pairs, [2..5]=stats, [6]=band pairs
+    // grid path
+    int64_t hcap;           // hash slots (power of two >= 2 cap_n)
+    int32_t hbits;
+    uint32_t *hkey;
+    int32_t *hcount;
+    int32_t *hval;
+    int32_t *hcursor;
+    int32_t *slot_of;       // hash slot of each point [cap_n]
+    float4 *pts4;           // {u0,u1,u2,-|u|^2} by point index [cap_n]
+    float4 *spts;           // same, grouped by cell [cap_n]
+    int32_t *sidx;          // point index of each grouped position [cap_n]
+    int32_t *scell;         // cell id of each grouped position [cap_n]
+    uint8_t *score;         // core flag of each grouped position [cap_n]
+    int32_t *cell_start, *cell_count, *cell_rep;  // [cap_n]
+    uint32_t *cell_key;     // [cap_n]
+    int32_t *nbr;           // neighbour-cell table [cap_n * noff_cap]
+    int32_t noff_cap;
+    // tensor-core path
+    uint16_t *h16;          // packed 16-bit operand tiles [cap_n_pad * 64]
+    int32_t *inorm;         // exact integer |v|^2 of the centred units [cap_n]
+    int32_t *list_a, *list_b;  // compacted index lists [cap_n]
+    int32_t *band;          // band pairs (p, q) awaiting exact recheck [band_cap * 2]
+    int64_t band_cap;
+    PhaseMarks *marks;      // host-side timing marks of the owning plan
+};
+
+// Host-side grid geometry for d <= 3 (see grid.cu).
+struct GridGeom {
+    int32_t d, c, G, Tc, noff, hbits;
+    float Tp1;
+    char4 off[124];
+};
+
+// ---- launchers (all enqueue on `st`; return cudaError_t of the launch) ----
+cudaError_t launch_prep_dense(const DbWork &w, const float *x, int64_t n, int32_t d, int32_t dp, cudaStream_t st);
+cudaError_t launch_allpairs_simt(const DbWork &w, int64_t n, int32_t d, int32_t dp, int64_t Tc, int32_t min_pts,
+                                 bool exact_counts, cudaStream_t st);
+cudaError_t launch_labels_allpairs(const DbWork &w, int64_t n, int32_t *labels, int32_t *counts_out,
+                                   uint8_t *core_out, cudaStream_t st);
+cudaError_t launch_compact(const DbWork &w, int64_t n, int32_t *labels, cudaStream_t st);
+cudaError_t launch_exclusive_scan(const int32_t *in, int32_t *out, int64_t n, int32_t *part, int64_t part_cap,
+                                  cudaStream_t st, PhaseMarks *pm);
+bool grid_geometry(int32_t d, int64_t Tc, int64_t n, GridGeom *g);
+cudaError_t launch_grid_path(const DbWork &w, const GridGeom &g, const float *x, int64_t n, int32_t min_pts,
+                             bool exact_counts, int32_t *labels, int32_t *counts_out, uint8_t *core_out,
+                             cudaStream_t st);
+cudaError_t launch_grid_candidates(const DbWork &w, const GridGeom &g, int64_t n, cudaStream_t st);
+cudaError_t launch_stats(const DbWork &w, int64_t n, const int32_t *labels, cudaStream_t st);
+int32_t dp_for(int32_t d);

@@ -1,0 +1,332 @@
+// pairs_simt.cu — all-pairs eps-test on the CUDA cores, fused with its consumer.
+//
+// Section IV-A tiles the pair loop through shared memory (each thread keeps its
+// own point in registers, a block stages TPB points at a time) and unrolls the
+// inner loop; Section IV-B fuses the distance test with the neighbour count, so
+// the distance matrix is never stored; Section IV-B's last step moves the
+// per-row terms out of the loop (the Gram form
+// dist = |t|^2 + |p|^2 - 2 t.p).  Here a 256-thread block owns a 64x64 tile of
+// (row, column) pairs; each thread scores a 4x4 micro-tile from shared memory.
+// The same tile loop feeds three consumers:
+//   PASS_COUNT   neighbour counts (step 2, core detection)
+//   PASS_UNION   union of core-core eps-edges (step 3, merging; Section IV-C)
+//   PASS_BORDER  smallest core neighbour of each non-core point
+//
+// Exact arithmetic.  The score of a pair is T + 1 - D(p,q), an integer, and q
+// is a neighbour iff score >= 1; __saturatef(score) is then exactly 0 or 1.
+//   MODE_GRAM   (d <= 8): score = (T+1 - |p|^2) - |q|^2 + sum_k (2u_pk) u_qk in
+//               FP32.  Every partial sum is an integer of magnitude below
+//               2*d*1023^2 <= 16,744,464 < 2^24, so FP32 holds it exactly.
+//   MODE_DIRECT (FP32, d <= 16, or T + 1 <= 2^24): score = (T+1) - sum (u_pk-u_qk)^2.
+//               Partial sums only decrease; they are exact while >= -2^24, and
+//               once below that they stay below 1, so the decision is exact.
+//   MODE_INT    otherwise: the same in int32.
+#include <climits>
+
+#include "internal.cuh"
+
+namespace {
+
+constexpr int BM = 64, BN = 64, NT = 256;
+enum { PASS_COUNT = 0, PASS_UNION = 1, PASS_BORDER = 2 };
+enum { MODE_GRAM = 0, MODE_DIRECT = 1, MODE_INT = 2 };
+
+struct ApArgs {
+    const float *P;  // packed units, row stride DP
+    int n;
+    float Tp1;       // T + 1 (exact: T + 1 <= 2^24 whenever a float mode is used)
+    int Tc;          // T clamped to d*1023^2
+    const uint8_t *core;
+    int *count;
+    int *parent;
+    int *border;
+    unsigned *status;
+    int ntiles;
+    int splits;
+};
+
+__global__ void prep_dense_kernel(const float *__restrict__ x, int64_t n, int d, int dp, float *__restrict__ P,
+                                  unsigned *status) {
+    const int64_t total = n * dp;
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = i / dp;
+        int k = (int)(i - r * dp);
+        float v = 0.f;
+        if (k < d) {
+            int u;
+            bad |= !db::on_grid(x[r * d + k], u);
+            v = (float)u;
+        }
+        P[i] = v;
+    }
+    if (bad) atomicOr(status, DB_EBIT_NOT_QUANTISED);
+}
+
+template <int DP, int MODE, int PASS>
+__global__ void __launch_bounds__(NT) ap_tile_kernel(ApArgs a) {
+    __shared__ __align__(16) float As[DP][BM];
+    __shared__ __align__(16) float Bs[DP][BN];
+    __shared__ float An[BM], Bn[BN];
+    __shared__ uint8_t Ac[BM], Bc[BN];
+
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int rt = blockIdx.x;
+    const int row0 = rt * BM;
+    const int first = (PASS == PASS_UNION) ? rt : 0;  // union: upper triangle only
+    const int span = a.ntiles - first;
+    const int per = (span + a.splits - 1) / a.splits;
+    const int ct_begin = first + blockIdx.y * per;
+    const int ct_end = min(a.ntiles, ct_begin + per);
+    if (ct_begin >= ct_end) return;
+
+    // ---- the row tile stays in shared memory for the whole block (Section IV-A) ----
+    for (int e = tid; e < BM * DP; e += NT) {
+        int r = e / DP, k = e - (e / DP) * DP;
+        int row = row0 + r;
+        As[k][r] = (row < a.n) ? a.P[(size_t)row * DP + k] : 0.f;
+    }
+    if (PASS != PASS_COUNT)
+        for (int r = tid; r < BM; r += NT) Ac[r] = (row0 + r < a.n) ? a.core[row0 + r] : 0;
+    __syncthreads();
+    if (MODE == MODE_GRAM) {
+        // Per-row terms hoisted out of the pair loop (Section IV-B): T+1-|p|^2 and 2p.
+        for (int r = tid; r < BM; r += NT) {
+            float nrm = 0.f;
+#pragma unroll
+            for (int k = 0; k < DP; ++k) {
+                float v = As[k][r];
+                nrm = fmaf(v, v, nrm);
+                As[k][r] = 2.f * v;
+            }
+            An[r] = a.Tp1 - nrm;
+        }
+    }
+    int want_rows = 1;
+    if (PASS == PASS_UNION || PASS == PASS_BORDER) {
+        int mine = 0;
+        for (int r = tid; r < BM; r += NT)
+            if (row0 + r < a.n) mine |= (PASS == PASS_UNION) ? (Ac[r] != 0) : (Ac[r] == 0);
+        want_rows = __syncthreads_or(mine);
+    } else {
+        __syncthreads();
+    }
+    if (!want_rows) return;
+
+    float rc[4] = {0.f, 0.f, 0.f, 0.f};
+    int bm[4] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX};
+
+    for (int ct = ct_begin; ct < ct_end; ++ct) {
+        const int col0 = ct * BN;
+        __syncthreads();
+        if (MODE == MODE_GRAM) {
+            if (tid < BN) {
+                const int col = col0 + tid;
+                float nrm = 0.f;
+                if (col < a.n) {
+#pragma unroll
+                    for (int k = 0; k < DP; ++k) {
+                        float v = a.P[(size_t)col * DP + k];
+                        Bs[k][tid] = v;
+                        nrm = fmaf(v, v, nrm);
+                    }
+                    Bn[tid] = -nrm;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < DP; ++k) Bs[k][tid] = 0.f;
+                    Bn[tid] = -1e30f;  // padding column: never a neighbour
+                }
+            }
+        } else {
+            for (int e = tid; e < BN * DP; e += NT) {
+                int c = e / DP, k = e - (e / DP) * DP;
+                int col = col0 + c;
+                Bs[k][c] = (col < a.n) ? a.P[(size_t)col * DP + k] : (MODE == MODE_INT ? 0.f : 1e18f);
+            }
+        }
+        int want_cols = 1;
+        if (PASS != PASS_COUNT) {
+            int mine = 0;
+            for (int c = tid; c < BN; c += NT) {
+                int col = col0 + c;
+                uint8_t f = (col < a.n) ? a.core[col] : 0;
+                Bc[c] = f;
+                mine |= f;
+            }
+            want_cols = __syncthreads_or(mine);
+        } else {
+            __syncthreads();
+        }
+        if (!want_cols) continue;
+
+        float acc[4][4];
+        int iacc[4][4];
+        if (MODE == MODE_GRAM) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = An[ty * 4 + i] + Bn[tx * 4 + j];
+        } else if (MODE == MODE_DIRECT) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = a.Tp1;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) iacc[i][j] = a.Tc;
+        }
+#pragma unroll
+        for (int k = 0; k < DP; ++k) {
+            const float4 av = *reinterpret_cast<const float4 *>(&As[k][ty * 4]);
+            const float4 bv = *reinterpret_cast<const float4 *>(&Bs[k][tx * 4]);
+            const float ar[4] = {av.x, av.y, av.z, av.w};
+            const float br[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (MODE == MODE_GRAM) {
+                        acc[i][j] = fmaf(ar[i], br[j], acc[i][j]);
+                    } else if (MODE == MODE_DIRECT) {
+                        float df = ar[i] - br[j];
+                        acc[i][j] = fmaf(-df, df, acc[i][j]);
+                    } else {
+                        int di = (int)ar[i] - (int)br[j];
+                        iacc[i][j] -= di * di;
+                    }
+                }
+        }
+        // ---- fused consumer (Section IV-B: no distance is stored) ----
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = ty * 4 + i, p = row0 + r;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = tx * 4 + j, q = col0 + c;
+                bool nb;
+                if (MODE == MODE_INT) nb = (iacc[i][j] >= 0) && (q < a.n);
+                else nb = acc[i][j] >= 1.f;
+                if (PASS == PASS_COUNT) {
+                    if (MODE == MODE_INT) rc[i] += nb ? 1.f : 0.f;
+                    else rc[i] += __saturatef(acc[i][j]);
+                } else if (PASS == PASS_UNION) {
+                    if (nb && p < q && Ac[r] && Bc[c]) db::uf_unite(a.parent, p, q, a.status);
+                } else {
+                    if (nb && p < a.n && !Ac[r] && Bc[c]) bm[i] = min(bm[i], q);
+                }
+            }
+        }
+    }
+
+    if (PASS == PASS_COUNT) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            int v = (int)rc[i];
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            const int p = row0 + ty * 4 + i;
+            if (tx == 0 && p < a.n && v) atomicAdd(a.count + p, v);
+        }
+    } else if (PASS == PASS_BORDER) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            int v = bm[i];
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+            const int p = row0 + ty * 4 + i;
+            if (tx == 0 && p < a.n && v != INT_MAX) atomicMin(a.border + p, v);
+        }
+    }
+}
+
+__global__ void core_init_kernel(int n, int min_pts, const int *__restrict__ count, uint8_t *__restrict__ core,
+                                 int *__restrict__ parent, int *__restrict__ border) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        core[i] = count[i] >= min_pts;
+        parent[i] = i;
+        border[i] = DB_NONE;
+    }
+}
+
+template <int DP, int MODE, int PASS>
+cudaError_t launch_pass(const ApArgs &a, const DbWork &w, cudaStream_t st) {
+    dim3 grid(a.ntiles, a.splits);
+    ap_tile_kernel<DP, MODE, PASS><<<grid, NT, 0, st>>>(a);
+    w.marks->kernel(PASS == PASS_COUNT ? "ap_count" : (PASS == PASS_UNION ? "ap_union" : "ap_border"), st);
+    return cudaGetLastError();
+}
+
+template <int DP, int MODE>
+cudaError_t run_passes(ApArgs a, const DbWork &w, int n, int min_pts, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(int32_t) * (size_t)n, st);
+    if (e) return e;
+    if ((e = launch_pass<DP, MODE, PASS_COUNT>(a, w, st))) return e;
+    core_init_kernel<<<min((n + 255) / 256, 4096), 256, 0, st>>>(n, min_pts, w.count, w.core, w.parent, w.border);
+    w.marks->kernel("core_init", st);
+    if ((e = cudaGetLastError())) return e;
+    if ((e = launch_pass<DP, MODE, PASS_UNION>(a, w, st))) return e;
+    return launch_pass<DP, MODE, PASS_BORDER>(a, w, st);
+}
+
+template <int DP>
+cudaError_t dispatch_mode(int mode, ApArgs a, const DbWork &w, int n, int min_pts, cudaStream_t st) {
+    if constexpr (DP <= 8) {
+        return run_passes<DP, MODE_GRAM>(a, w, n, min_pts, st);
+    } else {
+        if (mode == MODE_DIRECT) return run_passes<DP, MODE_DIRECT>(a, w, n, min_pts, st);
+        return run_passes<DP, MODE_INT>(a, w, n, min_pts, st);
+    }
+}
+
+}  // namespace
+
+int32_t dp_for(int32_t d) {
+    if (d <= 4) return d == 4 ? 4 : d;  // 1, 2, 3, 4
+    if (d <= 8) return 8;
+    if (d <= 16) return 16;
+    if (d <= 32) return 32;
+    if (d <= 64) return 64;
+    return -1;
+}
+
+cudaError_t launch_prep_dense(const DbWork &w, const float *x, int64_t n, int32_t d, int32_t dp, cudaStream_t st) {
+    int64_t total = n * dp;
+    int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
+    if (blocks < 1) blocks = 1;
+    prep_dense_kernel<<<blocks, 256, 0, st>>>(x, n, d, dp, w.P, w.status);
+    w.marks->kernel("prep_dense", st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_allpairs_simt(const DbWork &w, int64_t n64, int32_t d, int32_t dp, int64_t Tc, int32_t min_pts,
+                                 bool /*exact_counts*/, cudaStream_t st) {
+    const int n = (int)n64;
+    ApArgs a;
+    a.P = w.P;
+    a.n = n;
+    a.Tc = (int)Tc;
+    a.Tp1 = (float)(Tc + 1);
+    a.core = w.core;
+    a.count = w.count;
+    a.parent = w.parent;
+    a.border = w.border;
+    a.status = w.status;
+    a.ntiles = (n + BM - 1) / BM;
+    // Enough blocks to fill 152 SMs a few times over, splitting the column range.
+    int splits = (4 * 152 + a.ntiles - 1) / a.ntiles;
+    a.splits = std::max(1, std::min(splits, a.ntiles));
+    int mode = (d <= 8) ? MODE_GRAM : ((d <= 16 || Tc + 1 <= (1 << 24)) ? MODE_DIRECT : MODE_INT);
+    switch (dp) {
+        case 1: return dispatch_mode<1>(mode, a, w, n, min_pts, st);
+        case 2: return dispatch_mode<2>(mode, a, w, n, min_pts, st);
+        case 3: return dispatch_mode<3>(mode, a, w, n, min_pts, st);
+        case 4: return dispatch_mode<4>(mode, a, w, n, min_pts, st);
+        case 8: return dispatch_mode<8>(mode, a, w, n, min_pts, st);
+        case 16: return dispatch_mode<16>(mode, a, w, n, min_pts, st);
+        case 32: return dispatch_mode<32>(mode, a, w, n, min_pts, st);
+        case 64: return dispatch_mode<64>(mode, a, w, n, min_pts, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
