@@ -20,15 +20,20 @@
 //   prep     grid check, cell key, hash insert, per-cell count
 //   cells    occupied slot -> cell id and point range (block-aggregated)
 //   scatter  points grouped by cell
-//   nbrs     neighbour-cell table (cell x offset -> cell id or -1)
+//   nbrs     neighbour-cell table (cell x offset -> cell id or -1), adjacent
+//            offsets first
 //   count    neighbour counts -> core flags (Section IV-B).  A cell with at
 //            least min_pts points makes all its points core with no test; other
 //            points stop counting once they reach min_pts unless exact counts
 //            are requested.  Each cell records its smallest core index (rep).
 //   uinit    each core point hangs under its cell's rep (cells are cliques)
 //   union    neighbouring cells whose cores contain one eps-pair are united
-//            (Section IV-C's merge); a cell pair already in one set is skipped
-//   label    border points take their smallest-index core neighbour; labels
+//            (Section IV-C's merge), adjacent cells in one launch and the
+//            outer ring in a second; a cell pair already in one set is skipped
+//   border   each non-core point finds its smallest-index core neighbour
+//   label    labels from the union-find roots
+// The pair kernels give one warp to one cell at a time and walk candidate
+// cells' points 32 at a time, so neighbour loads are coalesced.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -203,43 +208,130 @@ __device__ __forceinline__ bool is_nbr(float cp, float px2, float py2, float pz2
     return acc >= 1.f;
 }
 
+// ---- warp-cooperative candidate scans -------------------------------------
+// A warp owns one cell A at a time.  The neighbour-cell table row of A is read
+// 32 entries at a time: lane l holds (start, size) of one neighbour cell and an
+// inclusive prefix of the sizes, so the candidates of those cells form one
+// flattened range that the 32 lanes walk together, 32 candidates per step.
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ int warp_incl_scan(int v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v += y;
+    }
+    return v;
+}
+
+__device__ __forceinline__ int warp_min(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(FULL, v, o));
+    return v;
+}
+
+// Position of flattened candidate j: smallest lane k with incl[k] > j (5-step
+// binary search over the lanes' prefixes), then start[k] + (j - exclusive[k]).
+// All 32 lanes must call it; the result is meaningless when j >= total.
+__device__ __forceinline__ int locate(int j, int incl, int c, int s) {
+    int k = 0;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1)
+        if (__shfl_sync(FULL, incl, k + step - 1) <= j) k += step;
+    k &= 31;
+    const int ik = __shfl_sync(FULL, incl, k), ck = __shfl_sync(FULL, c, k), sk = __shfl_sync(FULL, s, k);
+    return sk + (j - (ik - ck));
+}
+
+struct PairArgs {
+    GridGeom g;
+    const unsigned long long *ctr0;
+    const float4 *spts;
+    const int *sidx;
+    const int *cell_start, *cell_count, *cell_rep;
+    const unsigned *cell_key;
+    const int *nbr;
+};
+
+// Count pass (Section IV-B, fused pair test + count).  Per cell A:
+//   |A| >= min_pts and no exact counts: every point is core, no pair test;
+//   |A| >= 32 with exact counts: one lane per point, candidates broadcast;
+//   otherwise: per point, the warp walks the flattened candidates and stops
+//   once the count reaches min_pts (unless exact counts are asked for).
+// The smallest core index of A is written to cell_rep[A].
 template <int D>
-__global__ void grid_count_kernel(int n, GridGeom g, const float4 *__restrict__ spts, const int *__restrict__ sidx,
-                                  const int *__restrict__ scell, const int *__restrict__ cell_start,
-                                  const int *__restrict__ cell_count, const int *__restrict__ nbr, int min_pts,
-                                  int exact, uint8_t *__restrict__ score, int *cell_rep, int *__restrict__ counts_out,
-                                  uint8_t *__restrict__ core_out) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = p < n;
-    bool core = false;
-    int A = -1, orig = DB_NONE;
-    if (valid) {
-        A = scell[p];
-        orig = sidx[p];
-        int cnt = cell_count[A];  // the own cell is a clique: all of it is in the neighbourhood
-        if (exact || cnt < min_pts) {
-            const float4 pt = spts[p];
-            const float cp = g.Tp1 + pt.w, px2 = 2.f * pt.x, py2 = 2.f * pt.y, pz2 = 2.f * pt.z;
-            const int *row = nbr + (size_t)A * g.noff;
-            const int lim = exact ? INT_MAX : min_pts;  // early exit at min_pts (Section II def. 2)
-            for (int o = 0; o < g.noff && cnt < lim; ++o) {
-                const int B = row[o];
-                if (B < 0) continue;
-                const int s = cell_start[B], e = s + cell_count[B];
-                for (int q = s; q < e && cnt < lim; ++q) cnt += is_nbr<D>(cp, px2, py2, pz2, spts[q]);
+__global__ void __launch_bounds__(256) grid_count_kernel(PairArgs a, int min_pts, int exact, uint8_t *score,
+                                                         int *cell_rep, int *counts_out, uint8_t *core_out) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int ncells = (int)(*a.ctr0 >> 32);
+    const int lim = exact ? INT_MAX : min_pts;
+    const int noff = a.g.noff;
+    for (int A = warp; A < ncells; A += nwarps) {
+        const int sA = a.cell_start[A], cA = a.cell_count[A];
+        const int *row = a.nbr + (size_t)A * noff;
+        int minorig = DB_NONE;
+        if (cA >= lim) {
+            for (int i = lane; i < cA; i += 32) {
+                const int p = sA + i, o = a.sidx[p];
+                score[p] = 1;
+                if (core_out) core_out[o] = 1;
+                minorig = min(minorig, o);
+            }
+        } else if (cA >= 32) {
+            for (int i0 = 0; i0 < cA; i0 += 32) {
+                const int i = i0 + lane;
+                const bool v = i < cA;
+                const int p = sA + (v ? i : 0);
+                const float4 pt = a.spts[p];
+                const float cp = a.g.Tp1 + pt.w, px2 = 2.f * pt.x, py2 = 2.f * pt.y, pz2 = 2.f * pt.z;
+                int cnt = cA;
+                for (int o = 0; o < noff; ++o) {
+                    if (__all_sync(FULL, cnt >= lim || !v)) break;
+                    const int B = row[o];
+                    if (B < 0) continue;
+                    const int s = a.cell_start[B], e = s + a.cell_count[B];
+                    for (int q = s; q < e; ++q) cnt += is_nbr<D>(cp, px2, py2, pz2, a.spts[q]);
+                }
+                if (v) {
+                    const bool core = cnt >= min_pts;
+                    const int o = a.sidx[p];
+                    score[p] = core;
+                    if (counts_out) counts_out[o] = cnt;
+                    if (core_out) core_out[o] = core;
+                    if (core) minorig = min(minorig, o);
+                }
+            }
+        } else {
+            for (int i = 0; i < cA; ++i) {
+                const int p = sA + i;
+                const float4 pt = a.spts[p];
+                const float cp = a.g.Tp1 + pt.w, px2 = 2.f * pt.x, py2 = 2.f * pt.y, pz2 = 2.f * pt.z;
+                int cnt = cA;
+                for (int o0 = 0; o0 < noff && cnt < lim; o0 += 32) {
+                    const int B = (o0 + lane < noff) ? row[o0 + lane] : -1;
+                    const int s = B >= 0 ? a.cell_start[B] : 0, c = B >= 0 ? a.cell_count[B] : 0;
+                    const int incl = warp_incl_scan(c), total = __shfl_sync(FULL, incl, 31);
+                    for (int base = 0; base < total && cnt < lim; base += 32) {
+                        const int j = base + lane;
+                        const int q = locate(j, incl, c, s);
+                        const bool hit = j < total && is_nbr<D>(cp, px2, py2, pz2, a.spts[q]);
+                        cnt += __popc(__ballot_sync(FULL, hit));
+                    }
+                }
+                const bool core = cnt >= min_pts;
+                if (lane == 0) {
+                    const int o = a.sidx[p];
+                    score[p] = core;
+                    if (counts_out) counts_out[o] = cnt;
+                    if (core_out) core_out[o] = core;
+                }
+                if (core) minorig = min(minorig, a.sidx[p]);
             }
         }
-        core = cnt >= min_pts;
-        score[p] = core;
-        if (counts_out) counts_out[orig] = cnt;
-        if (core_out) core_out[orig] = core;
-    }
-    // Smallest core index per cell, one atomic per (warp, cell).
-    const unsigned cmask = __ballot_sync(0xffffffffu, core);
-    if (core) {
-        const unsigned peers = __match_any_sync(cmask, A);
-        const int m = (int)__reduce_min_sync(peers, (unsigned)orig);
-        if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicMin(cell_rep + A, m);
+        minorig = warp_min(minorig);
+        if (lane == 0) cell_rep[A] = minorig;
     }
 }
 
@@ -252,68 +344,116 @@ __global__ void grid_union_init_kernel(int n, const int *__restrict__ sidx, cons
     }
 }
 
+// Merge pass (Section IV-C).  The core points of one cell are already one set
+// (cells are cliques).  For each neighbouring cell B of A (from the smaller
+// key, offsets [o_begin, o_end)), if A and B are not yet in one set, the warp
+// searches for one core pair within eps — lanes over the larger cell, a loop
+// over the smaller — and unites the two cells at the first hit.
 template <int D>
-__global__ void grid_union_kernel(int n, GridGeom g, const float4 *__restrict__ spts, const int *__restrict__ scell,
-                                  const uint8_t *__restrict__ score, const int *__restrict__ cell_start,
-                                  const int *__restrict__ cell_count, const unsigned *__restrict__ cell_key,
-                                  const int *__restrict__ cell_rep, const int *__restrict__ nbr, int *parent,
-                                  unsigned *status) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n || !score[p]) return;
-    const int A = scell[p];
-    const unsigned keyA = cell_key[A];
-    const int repA = cell_rep[A];
-    const float4 pt = spts[p];
-    const float cp = g.Tp1 + pt.w, px2 = 2.f * pt.x, py2 = 2.f * pt.y, pz2 = 2.f * pt.z;
-    const int *row = nbr + (size_t)A * g.noff;
-    for (int o = 0; o < g.noff; ++o) {
-        const int B = row[o];
-        if (B < 0 || cell_key[B] < keyA) continue;  // each cell pair from its smaller key
-        const int repB = cell_rep[B];
-        if (repB == DB_NONE) continue;
-        if (db::uf_find(parent, repA) == db::uf_find(parent, repB)) continue;
-        const int s = cell_start[B], e = s + cell_count[B];
-        for (int q = s; q < e; ++q) {
-            if (score[q] && is_nbr<D>(cp, px2, py2, pz2, spts[q])) {
-                db::uf_unite(parent, repA, repB, status);
-                break;
+__global__ void __launch_bounds__(256) grid_union_kernel(PairArgs a, const uint8_t *__restrict__ score, int *parent,
+                                                         unsigned *status, int o_begin, int o_end) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int ncells = (int)(*a.ctr0 >> 32);
+    for (int A = warp; A < ncells; A += nwarps) {
+        const int repA = a.cell_rep[A];
+        if (repA == DB_NONE) continue;
+        const unsigned keyA = a.cell_key[A];
+        const int sA = a.cell_start[A], cA = a.cell_count[A];
+        const int *row = a.nbr + (size_t)A * a.g.noff;
+        for (int o = o_begin; o < o_end; ++o) {
+            const int B = row[o];
+            if (B < 0 || a.cell_key[B] < keyA) continue;
+            const int repB = a.cell_rep[B];
+            if (repB == DB_NONE) continue;
+            if (db::uf_find(parent, repA) == db::uf_find(parent, repB)) continue;
+            const int sB = a.cell_start[B], cB = a.cell_count[B];
+            const bool swap = cB > cA;  // lanes over the larger cell
+            const int sX = swap ? sB : sA, cX = swap ? cB : cA, sY = swap ? sA : sB, cY = swap ? cA : cB;
+            bool found = false;
+            for (int x0 = 0; x0 < cX && !found; x0 += 32) {
+                const int xi = x0 + lane;
+                const bool vx = xi < cX && score[sX + xi];
+                if (!__any_sync(FULL, vx)) continue;
+                const float4 px = a.spts[sX + (xi < cX ? xi : 0)];
+                const float cp = a.g.Tp1 + px.w, px2 = 2.f * px.x, py2 = 2.f * px.y, pz2 = 2.f * px.z;
+                for (int y = sY; y < sY + cY; ++y) {
+                    if (!score[y]) continue;
+                    const bool hit = vx && is_nbr<D>(cp, px2, py2, pz2, a.spts[y]);
+                    if (__any_sync(FULL, hit)) {
+                        found = true;
+                        break;
+                    }
+                }
             }
+            if (found && lane == 0) db::uf_unite(parent, repA, repB, status);
+            __syncwarp();
         }
     }
 }
 
+// Border pass: each non-core point takes its smallest-index core neighbour
+// (the reading used for points reachable from several clusters).  Only cells
+// with fewer than min_pts points hold non-core points.  The own cell's
+// representative is a neighbour (cliques); other cells are skipped when their
+// representative (their smallest core index) cannot beat the current best.
 template <int D>
-__global__ void grid_label_kernel(int n, GridGeom g, const float4 *__restrict__ spts, const int *__restrict__ sidx,
-                                  const int *__restrict__ scell, const uint8_t *__restrict__ score,
-                                  const int *__restrict__ cell_start, const int *__restrict__ cell_count,
-                                  const int *__restrict__ cell_rep, const int *__restrict__ nbr, int *parent,
-                                  int *__restrict__ labels, unsigned long long *ctr) {
+__global__ void __launch_bounds__(256) grid_border_kernel(PairArgs a, int min_pts, const uint8_t *__restrict__ score,
+                                                          int *__restrict__ bord) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int ncells = (int)(*a.ctr0 >> 32);
+    const int noff = a.g.noff;
+    for (int A = warp; A < ncells; A += nwarps) {
+        const int sA = a.cell_start[A], cA = a.cell_count[A];
+        if (cA >= min_pts) continue;
+        const int repA = a.cell_rep[A];
+        const int *row = a.nbr + (size_t)A * noff;
+        for (int i = 0; i < cA; ++i) {
+            const int p = sA + i;
+            if (score[p]) continue;
+            const float4 pt = a.spts[p];
+            const float cp = a.g.Tp1 + pt.w, px2 = 2.f * pt.x, py2 = 2.f * pt.y, pz2 = 2.f * pt.z;
+            int b = repA;
+            for (int o0 = 0; o0 < noff; o0 += 32) {
+                const int B = (o0 + lane < noff) ? row[o0 + lane] : -1;
+                const bool useful = B >= 0 && a.cell_rep[B] < b;
+                const int s = useful ? a.cell_start[B] : 0, c = useful ? a.cell_count[B] : 0;
+                const int incl = warp_incl_scan(c), total = __shfl_sync(FULL, incl, 31);
+                int best = b;
+                for (int base = 0; base < total; base += 32) {
+                    const int j = base + lane;
+                    const int q = locate(j, incl, c, s);
+                    if (j < total && score[q]) {
+                        const int qi = a.sidx[q];
+                        if (qi < best && is_nbr<D>(cp, px2, py2, pz2, a.spts[q])) best = qi;
+                    }
+                }
+                b = warp_min(best);
+            }
+            if (lane == 0) bord[p] = b;
+        }
+    }
+}
+
+// Labels: a core point takes its set's root (its cluster's smallest core
+// index); a border point the root of its chosen core neighbour; noise -1.
+__global__ void grid_label_kernel(int n, const int *__restrict__ sidx, const uint8_t *__restrict__ score,
+                                  const int *__restrict__ scell, const int *__restrict__ cell_count, int min_pts,
+                                  const int *__restrict__ bord, int *parent, int *__restrict__ labels,
+                                  unsigned long long *ctr) {
     __shared__ int red[4][32];
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     int nc = 0, nb = 0, nn = 0, nr = 0;
     if (p < n) {
         const int orig = sidx[p];
-        const int A = scell[p];
         int lab;
         if (score[p]) {
             lab = db::uf_find(parent, orig);
             nc = 1;
             nr = lab == orig;
         } else {
-            int b = cell_rep[A];  // own-cell cores are all neighbours; the rep is the smallest
-            const float4 pt = spts[p];
-            const float cp = g.Tp1 + pt.w, px2 = 2.f * pt.x, py2 = 2.f * pt.y, pz2 = 2.f * pt.z;
-            const int *row = nbr + (size_t)A * g.noff;
-            for (int o = 0; o < g.noff; ++o) {
-                const int B = row[o];
-                if (B < 0 || cell_rep[B] >= b) continue;  // cannot beat b
-                const int s = cell_start[B], e = s + cell_count[B];
-                for (int q = s; q < e; ++q) {
-                    if (!score[q]) continue;
-                    const int qi = sidx[q];
-                    if (qi < b && is_nbr<D>(cp, px2, py2, pz2, spts[q])) b = qi;
-                }
-            }
+            const int b = bord[p];
             if (b == DB_NONE) {
                 lab = -1;
                 nn = 1;
@@ -324,12 +464,11 @@ __global__ void grid_label_kernel(int n, GridGeom g, const float4 *__restrict__ 
         }
         labels[orig] = lab;
     }
-    // block-reduced statistics
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int v[4] = {nc, nb, nn, nr};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(FULL, v[k], o);
         if (lane == 0) red[k][wid] = v[k];
     }
     __syncthreads();
@@ -375,17 +514,23 @@ int64_t isqrt64(int64_t v) {
 template <int D>
 cudaError_t grid_pair_passes(const DbWork &w, const GridGeom &g, int n, int min_pts, bool exact, int32_t *labels,
                              int32_t *counts_out, uint8_t *core_out, cudaStream_t st) {
-    const int nb = (n + 255) / 256;
-    grid_count_kernel<D><<<nb, 256, 0, st>>>(n, g, w.spts, w.sidx, w.scell, w.cell_start, w.cell_count, w.nbr,
-                                             min_pts, exact ? 1 : 0, w.score, w.cell_rep, counts_out, core_out);
+    PairArgs a{g, w.ctr, w.spts, w.sidx, w.cell_start, w.cell_count, w.cell_rep, w.cell_key, w.nbr};
+    const int wgrid = 152 * 16;  // 8 warps per block, warps stride over the cells
+    grid_count_kernel<D><<<wgrid, 256, 0, st>>>(a, min_pts, exact ? 1 : 0, w.score, w.cell_rep, counts_out, core_out);
     w.marks->kernel("grid_count", st);
+    const int nb = (n + 255) / 256;
     grid_union_init_kernel<<<nb, 256, 0, st>>>(n, w.sidx, w.scell, w.score, w.cell_rep, w.parent);
     w.marks->kernel("grid_union_init", st);
-    grid_union_kernel<D><<<nb, 256, 0, st>>>(n, g, w.spts, w.scell, w.score, w.cell_start, w.cell_count,
-                                             w.cell_key, w.cell_rep, w.nbr, w.parent, w.status);
-    w.marks->kernel("grid_union", st);
-    grid_label_kernel<D><<<nb, 256, 0, st>>>(n, g, w.spts, w.sidx, w.scell, w.score, w.cell_start, w.cell_count,
-                                             w.cell_rep, w.nbr, w.parent, labels, w.ctr);
+    grid_union_kernel<D><<<wgrid, 256, 0, st>>>(a, w.score, w.parent, w.status, 0, g.nnear);
+    w.marks->kernel("grid_union_near", st);
+    if (g.noff > g.nnear) {
+        grid_union_kernel<D><<<wgrid, 256, 0, st>>>(a, w.score, w.parent, w.status, g.nnear, g.noff);
+        w.marks->kernel("grid_union_far", st);
+    }
+    grid_border_kernel<D><<<wgrid, 256, 0, st>>>(a, min_pts, w.score, w.border);
+    w.marks->kernel("grid_border", st);
+    grid_label_kernel<<<nb, 256, 0, st>>>(n, w.sidx, w.score, w.scell, w.cell_count, min_pts, w.border, w.parent,
+                                          labels, w.ctr);
     w.marks->kernel("grid_label", st);
     return cudaGetLastError();
 }
@@ -423,6 +568,14 @@ bool grid_geometry(int32_t d, int64_t Tc, int64_t n, GridGeom *g) {
                 g->off[k++] = make_char4((signed char)ox, (signed char)oy, (signed char)oz, 0);
             }
     g->noff = k;
+    // Adjacent cells (every |o_k| <= 1) first: the merge pass runs them before the
+    // outer ring, which then mostly finds its cell pairs already united.
+    std::stable_partition(g->off, g->off + k, [](char4 o) {
+        return std::abs(o.x) <= 1 && std::abs(o.y) <= 1 && std::abs(o.z) <= 1;
+    });
+    int nn = 0;
+    while (nn < k && std::abs(g->off[nn].x) <= 1 && std::abs(g->off[nn].y) <= 1 && std::abs(g->off[nn].z) <= 1) ++nn;
+    g->nnear = nn;
     return true;
 }
 

@@ -156,7 +156,7 @@ struct DbWork {
 
 // Host-side grid geometry for d <= 3 (see grid.cu).
 struct GridGeom {
-    int32_t d, c, G, Tc, noff, hbits;
+    int32_t d, c, G, Tc, noff, nnear, hbits;
     float Tp1;
     char4 off[124];
 };
