@@ -208,6 +208,30 @@ int dbscan_serve_poll(dbscan_server *srv, uint64_t job_id, int32_t *done);
 int dbscan_serve_wait(dbscan_server *srv, uint64_t job_id, int64_t timeout_us, double *latency_us);
 int dbscan_serve_destroy(dbscan_server *srv);
 
+/* ---- Entry point that allocates nothing (the paper has no counterpart) ----
+ *
+ * For callers that cannot call cudaMalloc: a process that reserved all device
+ * memory for its own pool up front, code that may not take the allocator's
+ * locks while other work runs, a fixed memory budget.  Clusters one instance
+ * like dbscan_run with the all-pairs CUDA-core path, taking its scratch from a
+ * fixed array in the library's device image (about 1.3 MiB, held on every GPU
+ * that loads the library until exit) instead of a plan.
+ *   points     device, row-major float32 [n][d], on the 2^-10 grid in [0,1)
+ *   n, d       0 <= n <= DBSCAN_NOALLOC_MAX_N, 1 <= d <= DBSCAN_NOALLOC_MAX_D;
+ *              larger sizes return DBSCAN_ERR_ARG
+ *   label_mode DBSCAN_LABEL_ROOT_INDEX or DBSCAN_LABEL_COMPACT
+ *   labels_out device int32 [n]
+ *   stream     cudaStream_t (NULL = legacy default stream); the call waits for it
+ * Runs on the calling thread's current device.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) and caches it, so
+ * make that first call before any stream capture.  All calls share the one
+ * array: calls whose work overlaps on the GPU race and must not be issued.
+ * Returns DBSCAN_ERR_NOT_QUANTISED for off-grid input. */
+#define DBSCAN_NOALLOC_MAX_N 16384
+#define DBSCAN_NOALLOC_MAX_D 16
+int dbscan_run_noalloc(const float *points, int64_t n, int32_t d, float eps, int32_t min_pts, int32_t label_mode,
+                       int32_t *labels_out, void *stream);
+
 /* Static description of a status code. */
 const char *dbscan_strerror(int status);
 

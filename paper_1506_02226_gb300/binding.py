@@ -76,6 +76,7 @@ _SIGS = {
     "dbscan_serve_poll": (ctypes.c_int, [c_p, ctypes.c_uint64, c_p]),
     "dbscan_serve_wait": (ctypes.c_int, [c_p, ctypes.c_uint64, c_i64, c_p]),
     "dbscan_serve_destroy": (ctypes.c_int, [c_p]),
+    "dbscan_run_noalloc": (ctypes.c_int, [c_p, c_i64, c_i32, c_f32, c_i32, c_i32, c_p, c_p]),
     "dbscan_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "dbscan_abi_version": (c_i32, []),
 }
@@ -184,6 +185,16 @@ def dbscan_batch(plan: int, instances, per_inst=None) -> int:
     """instances: a ctypes array of dbscan_instance; per_inst: ctypes array of dbscan_stats or None."""
     return lib().dbscan_batch(plan, ctypes.cast(instances, c_p), len(instances),
                               ctypes.cast(per_inst, c_p) if per_inst is not None else None)
+
+
+DBSCAN_NOALLOC_MAX_N = 16384
+DBSCAN_NOALLOC_MAX_D = 16
+
+
+def dbscan_run_noalloc(points: int, n: int, d: int, eps: float, min_pts: int, label_mode: int, labels_out: int,
+                       stream: int | None = None) -> int:
+    """Status code of the call; clusters without any device allocation (see include/dbscan.h)."""
+    return lib().dbscan_run_noalloc(points, n, d, eps, min_pts, label_mode, labels_out, stream)
 
 
 def dbscan_serve_opts_default() -> dbscan_serve_opts:
