@@ -130,29 +130,54 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "src": "fallback"}
 
 
-def algorithmic_work(name: str, n: int, d: int, st: dict):
-    """(bound, work per launch, unit) of a kernel: bytes it must move at least,
-    counted from the data it reads and writes once (HBM-bound kernels)."""
-    cells = max(st.get("cells", 0), 1)
+def grid_offsets(d: int, T: int):
+    """Cell side and neighbour offsets of the eps-grid (same rule as the library)."""
+    import itertools
+    c = math.isqrt(T // d) + 1
+    r = -(-math.isqrt(T) // c)
+    offs = [o for o in itertools.product(range(-r, r + 1), repeat=d)
+            if any(o) and sum(((abs(x) - 1) * c + 1) ** 2 for x in o if x) <= T]
+    return c, offs
+
+
+def algorithmic_work(name: str, n: int, d: int, eps: float, st: dict):
+    """(bound, bytes per launch) of a kernel: the bytes it has to move at least,
+    counting every input it must read and every output it must write once.
+
+    Grid kernels (per point unless marked): prep reads x (4d) and writes the
+    packed point (16) and hash slot (4), touching one hash entry (8); cells reads
+    the hash table (8 per slot) and writes 24 per cell; scatter reads slot,
+    cursor, cell id and packed point (28) and writes packed point, index and
+    cell id (24); nbrs reads a cell key (4) and a hash entry (8) and writes a
+    table entry (4) per (cell, offset); count reads index (4), writes core flag
+    (1) and parent (4), plus 12 per cell and its table row (4 per offset);
+    union reads per cell 16 bytes and its table row, plus 16 per neighbouring
+    cell; border reads the index and flag of non-core points' cells; label
+    reads index and flag (5) and writes the label (4), plus 16 per cell.
+    """
+    e = float(np.float32(eps))
+    T = min(math.floor(e * e * 1048576.0), d * 1023 * 1023)
+    cells = max(int(st.get("cells", 0)), 1)
+    H = 1 << max(10, math.ceil(math.log2(2 * n)))
+    if d <= 3:
+        _, offs = grid_offsets(d, T)
+        noff = len(offs)
+    else:
+        noff = 0
     table = {
-        # x (4d) in; slot (4) + packed point (16) out; one hash read/atomic (8) per point
-        "grid_prep": 4 * d + 4 + 16 + 8,
-        # slot (4), cursor atomic (4), cell id (4), packed point (16) in; point, index, cell (24) out
-        "grid_scatter": 4 + 4 + 4 + 16 + 24,
-        # cell id, index, cell size, packed point in (28); core flag (1) out
-        "grid_count": 28 + 1,
-        # cell id, index, flag, rep in (13); parent (4) out
-        "grid_union_init": 13 + 4,
-        # index, cell, flag (9) in; parent chain (8) + label (4)
-        "grid_label": 9 + 8 + 4,
+        "grid_prep": (4 * d + 28) * n,
+        "grid_cells": 8 * H + 24 * cells,
+        "grid_scatter": 52 * n,
+        "grid_nbrs": 16 * cells * noff,
+        "grid_count": 9 * n + (12 + 4 * noff) * cells,
+        "grid_union_near": (16 + 4 * noff + 16 * noff) * cells,
+        "grid_union_far": (16 + 4 * noff + 16 * noff) * cells,
+        "grid_border": 5 * n,
+        "grid_label": 9 * n + 16 * cells,
     }
     if name in table:
-        return "hbm", table[name] * n, "GB/s"
-    if name == "grid_cells":
-        return "hbm", 0, "GB/s"
-    if name == "grid_nbrs":
-        return "hbm", 0, "GB/s"
-    return None, 0, None
+        return "hbm", table[name]
+    return None, 0
 
 
 # ------------------------------------------------------------------ arms
@@ -284,7 +309,7 @@ def run_ours(args, wl_name):
     for _ in range(2):
         eplan.run_host(host_pts, inst.eps, inst.min_pts, labels=host_lab)
     e2e_s = []
-    for _ in range(max(3, args.steps // 4)):
+    for _ in range(max(3, args.steps // 4) if not args.no_baseline else 1):
         flush.fill_(1)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -302,17 +327,16 @@ def run_ours(args, wl_name):
     avg = {k: statistics.mean(v) for k, v in kern.items()}
     dom = max(avg, key=avg.get)
     peaks = load_peaks()
-    bound, work, unit = algorithmic_work(dom, n, d, st0)
-    roof = None
+    bound, work = algorithmic_work(dom, n, d, inst.eps, st0)
     if bound == "hbm" and work:
         ach = work / (avg[dom] * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_src": peaks["src"],
+                "frac": ach / peaks["hbm_gbs"], "traffic": args.traffic, "peak_src": peaks["src"],
                 "algorithmic_bytes": work, "avg_ms": avg[dom]}
     else:
-        roof = {"kernel": dom, "bound": bound, "achieved": None, "peak": None, "unit": unit, "frac": None,
+        roof = {"kernel": dom, "bound": bound, "achieved": None, "peak": None, "unit": None, "frac": None,
                 "traffic": None, "avg_ms": avg[dom]}
-    cpu = cpu_baseline(inst, wl_name, desc)
+    cpu = cpu_baseline(inst, wl_name, desc) if not args.no_baseline else None
     out = {
         "metric": "G pair-tests/s", "value": value, "unit": "G pair-tests/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -343,6 +367,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="lowd2")
+    ap.add_argument("--no-baseline", action="store_true", help="skip the CPU baseline (for profiler runs)")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per launch of the dominant kernel from an ncu capture, for the roofline")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -163,6 +163,23 @@ int dbscan_plan_sync(dbscan_plan *plan);
  * string naming it (nullable arrays); *count receives the number of kernels. */
 int dbscan_plan_phase_times(dbscan_plan *plan, int32_t max_phases, float *ms, const char **names, int32_t *count);
 
+/* Check of the tensor-core pair test's rounding band (Section IV-B's Gram
+ * form on FP16/BF16 tensor cores): runs the count pass over all n^2 pairs of
+ * `points` (device, row-major float32 [n][d], d <= 64) deciding every pair
+ * both the fast way and exactly in int32, and reports what it saw.  For
+ * diagnosis and tests (it is slow: an exact recheck per pair).  The plan needs
+ * max_d >= 16.  bf16 = 0 checks FP16 operands, 1 BF16. */
+typedef struct dbscan_tc_report {
+    int64_t pairs;              /* ordered pairs examined (n^2) */
+    int64_t band_pairs;         /* pairs inside the band, which the fast path rechecks */
+    int64_t wrong_outside_band; /* pairs outside the band decided differently from exact: must be 0 */
+    int64_t max_abs_error_2g;   /* largest |2G_tensor - 2G_exact| seen, in squared grid units */
+    int64_t band_halfwidth_2g;  /* FP16 band half-width in the same units (-1: per-pair, BF16) */
+    int64_t threshold;          /* T */
+} dbscan_tc_report;
+int dbscan_tc_verify(dbscan_plan *plan, const float *points, int64_t n, int32_t d, float eps, int32_t bf16,
+                     dbscan_tc_report *out);
+
 /* Device bytes the plan's workspace holds. */
 int64_t dbscan_plan_workspace_bytes(const dbscan_plan *plan);
 

@@ -54,6 +54,14 @@ class dbscan_instance(ctypes.Structure):
                 ("labels_out", c_p)]
 
 
+class dbscan_tc_report(ctypes.Structure):
+    _fields_ = [("pairs", c_i64), ("band_pairs", c_i64), ("wrong_outside_band", c_i64),
+                ("max_abs_error_2g", c_i64), ("band_halfwidth_2g", c_i64), ("threshold", c_i64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class dbscan_serve_opts(ctypes.Structure):
     _fields_ = [("device", c_i32), ("slots", c_i32), ("hbm_budget_bytes", c_i64), ("label_mode", c_i32),
                 ("precision", c_i32), ("reserved", c_i32 * 8)]
@@ -68,6 +76,7 @@ _SIGS = {
     "dbscan_run_host": (ctypes.c_int, [c_p, c_p, c_i64, c_i32, c_f32, c_i32, c_p, c_p]),
     "dbscan_plan_sync": (ctypes.c_int, [c_p]),
     "dbscan_plan_workspace_bytes": (c_i64, [c_p]),
+    "dbscan_tc_verify": (ctypes.c_int, [c_p, c_p, c_i64, c_i32, c_f32, c_i32, c_p]),
     "dbscan_plan_phase_times": (ctypes.c_int, [c_p, c_i32, c_p, c_p, c_p]),
     "dbscan_batch": (ctypes.c_int, [c_p, c_p, c_i32, c_p]),
     "dbscan_serve_opts_default": (None, [c_p]),
@@ -175,6 +184,12 @@ def dbscan_plan_phase_times(plan: int, max_phases: int = 32) -> list[tuple[str, 
     _check(lib().dbscan_plan_phase_times(plan, max_phases, ms, names, ctypes.byref(cnt)), "dbscan_plan_phase_times")
     k = min(cnt.value, max_phases)
     return [(names[i].decode(), float(ms[i])) for i in range(k)]
+
+
+def dbscan_tc_verify(plan: int, points: int, n: int, d: int, eps: float, bf16: int) -> dict:
+    rep = dbscan_tc_report()
+    _check(lib().dbscan_tc_verify(plan, points, n, d, eps, bf16, ctypes.byref(rep)), "dbscan_tc_verify")
+    return rep.as_dict()
 
 
 def dbscan_plan_workspace_bytes(plan: int) -> int:

@@ -78,6 +78,23 @@ size_t layout(DbWork &w, const dbscan_opts &o, char *base) {
         w.hcap = 0;
         w.noff_cap = 0;
     }
+    if (o.max_d >= 16) {
+        const int64_t np = (n + 255) / 256 * 256;
+        w.tc_cap_pad = np;
+        w.v16 = c.take<int16_t>((size_t)n * 64);
+        w.inorm = c.take<int32_t>(n);
+        w.opAll = c.take<uint16_t>((size_t)np * 64);
+        w.opCore = c.take<uint16_t>((size_t)np * 64);
+        w.opNon = c.take<uint16_t>((size_t)np * 64);
+        w.metaAll = c.take<char>((size_t)np * 16);
+        w.metaCore = c.take<char>((size_t)np * 16);
+        w.metaNon = c.take<char>((size_t)np * 16);
+        w.list_a = c.take<int32_t>(n);
+        w.list_b = c.take<int32_t>(n);
+        w.tc_lens = c.take<int32_t>(4);
+    } else {
+        w.tc_cap_pad = 0;
+    }
     return align_up(c.off, 256);
 }
 
@@ -148,13 +165,22 @@ int plan_run(dbscan_plan *plan, const float *points, int64_t n, int32_t d, float
         path = DBSCAN_PATH_GRID;
         err = launch_grid_path(plan->w, g, points, n, min_pts, exact, labels, counts_out, core_out, st);
     } else {
-        if (o.precision == DBSCAN_PREC_FP16_GRAM || o.precision == DBSCAN_PREC_BF16_GRAM)
-            return DBSCAN_ERR_UNSUPPORTED;
-        const int dp = dp_for(d);
-        if (dp < 0) return DBSCAN_ERR_UNSUPPORTED;
-        path = DBSCAN_PATH_ALLPAIRS_SIMT;
-        err = launch_prep_dense(plan->w, points, n, d, dp, st);
-        if (!err) err = launch_allpairs_simt(plan->w, n, d, dp, Tc, min_pts, exact, st);
+        const bool tc_ok = plan->w.tc_cap_pad > 0 && d <= 64 && Tc < (1 << 24);
+        const bool want_tc = o.precision == DBSCAN_PREC_FP16_GRAM || o.precision == DBSCAN_PREC_BF16_GRAM ||
+                             (o.precision == DBSCAN_PREC_AUTO && d >= 16 && n >= 4096);
+        if (want_tc && !tc_ok) {
+            if (o.precision != DBSCAN_PREC_AUTO) return DBSCAN_ERR_UNSUPPORTED;
+        }
+        if (want_tc && tc_ok) {
+            path = DBSCAN_PATH_ALLPAIRS_TC;
+            err = launch_allpairs_tc(plan->w, points, n, d, Tc, min_pts, o.precision == DBSCAN_PREC_BF16_GRAM, st);
+        } else {
+            const int dp = dp_for(d);
+            if (dp < 0) return DBSCAN_ERR_UNSUPPORTED;
+            path = DBSCAN_PATH_ALLPAIRS_SIMT;
+            err = launch_prep_dense(plan->w, points, n, d, dp, st);
+            if (!err) err = launch_allpairs_simt(plan->w, n, d, dp, Tc, min_pts, exact, st);
+        }
         if (!err) err = launch_labels_allpairs(plan->w, n, labels, counts_out, core_out, st);
     }
     if (!err && o.label_mode == DBSCAN_LABEL_COMPACT) err = launch_compact(plan->w, n, labels, st);
@@ -330,6 +356,34 @@ int dbscan_plan_phase_times(dbscan_plan *plan, int32_t max_phases, float *ms, co
         if (names) names[i] = plan->marks.name[i];
     }
     if (count) *count = plan->marks.n;
+    return DBSCAN_OK;
+}
+
+int dbscan_tc_verify(dbscan_plan *plan, const float *points, int64_t n, int32_t d, float eps, int32_t bf16,
+                     dbscan_tc_report *out) {
+    if (!plan || !out || !points || n < 1 || n > plan->w.cap_n || d < 1 || d > 64 || !(eps > 0.0f) ||
+        std::isinf(eps))
+        return DBSCAN_ERR_ARG;
+    if (plan->w.tc_cap_pad == 0) return DBSCAN_ERR_UNSUPPORTED;
+    const double e = (double)eps;
+    const int64_t T = std::min<int64_t>((int64_t)std::floor(e * e * 1048576.0), (int64_t)d * 1023 * 1023);
+    if (T >= (1 << 24)) return DBSCAN_ERR_UNSUPPORTED;
+    DeviceGuard dg(plan->opts.device);
+    cudaStream_t st = plan->stream;
+    if (cudaMemsetAsync(plan->w.ctr, 0, sizeof(unsigned long long) * 16, st) != cudaSuccess) return DBSCAN_ERR_CUDA;
+    if (cudaMemsetAsync(plan->w.status, 0, sizeof(unsigned), st) != cudaSuccess) return DBSCAN_ERR_CUDA;
+    if (launch_tc_verify(plan->w, points, n, d, T, bf16 != 0, st) != cudaSuccess) return DBSCAN_ERR_CUDA;
+    if (cudaMemcpyAsync(plan->h_ctr, plan->w.ctr, sizeof(unsigned long long) * 16, cudaMemcpyDeviceToHost, st) !=
+        cudaSuccess)
+        return DBSCAN_ERR_CUDA;
+    const int s = plan_read_status(plan, true);
+    if (s) return s;
+    out->pairs = n * n;
+    out->band_pairs = (int64_t)plan->h_ctr[6];
+    out->wrong_outside_band = (int64_t)plan->h_ctr[7];
+    out->max_abs_error_2g = (int64_t)plan->h_ctr[8];
+    out->band_halfwidth_2g = bf16 ? -1 : 8;
+    out->threshold = T;
     return DBSCAN_OK;
 }
 

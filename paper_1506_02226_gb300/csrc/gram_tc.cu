@@ -1,0 +1,708 @@
+// gram_tc.cu — tensor-core Gram form of the pair test (tcgen05, sm_103a).
+//
+// Section IV-B of the paper rewrites the squared distance as
+//   dist(t, p) = |t|^2 + |p|^2 - 2 t.p
+// and hoists the per-point terms out of the loop.  For d >= 16 the dot
+// products t.p of a 128 x 256 tile of pairs are one dense contraction, so they
+// run on the 5th-generation tensor cores: tcgen05.mma with FP16 or BF16
+// operands staged in shared memory and an FP32 accumulator in tensor memory.
+//
+// Exactness.  Coordinates are centred, v = u - 512 in [-512, 511]:
+//   FP16 holds every v exactly, products are exact, and for d <= 64 every
+//   partial sum of G = v_p . v_q is an integer of magnitude <= 64 * 2^18 =
+//   2^24, so FP32 accumulation leaves G exact.  Then, with beta_q = |v_q|^2 and
+//   alpha_p = |v_p|^2 - T (both exact integers, |.| <= 2^24 because T < 2^24),
+//   w = fma(2, G, -beta_q) rounds at most once, and w >= alpha_p decides
+//   D(p,q) <= T exactly: when |2G - beta| > 2^24 the rounded w stays on the
+//   same side of alpha.  Pairs with |w - alpha| <= FP16_BAND are still
+//   rechecked in int32 arithmetic, so the labels stay exact even if the
+//   hardware accumulation were less precise than assumed.
+//   BF16 (8-bit significand) rounds v, each by at most 2^-8 |v|, so
+//   |G_bf16 - G| <= e |v_p| |v_q| with e = 2^-7 + 2^-16 (Cauchy-Schwarz); the
+//   products of the rounded integers are still integers, so accumulation adds
+//   no error.  A pair is decided directly when |w - alpha| > 2 e |v_p||v_q|
+//   (per-row and per-column factors rho = sqrt(2e) |v| (1 + 2^-10)), and
+//   rechecked exactly otherwise.
+//
+// Data layout.  Each operand list (all points, core points, non-core points)
+// is packed once into 128-row tiles in the canonical K-major layout without
+// swizzle: 8 x 8 core matrices of 128 contiguous bytes, K-adjacent core
+// matrices 128 B apart (leading byte offset) and 8-row groups KG*128 B apart
+// (stride byte offset).  A 128-row A tile or a 256-row B tile is therefore one
+// contiguous block, fetched by a single cp.async.bulk (TMA) copy.  Per-point
+// metadata {beta, rho, index} rides along in the same copy group.
+//
+// CTA roles (320 threads, one CTA per SM, persistent over work items):
+//   warp 0      producer: bulk copies of A tiles (2 buffers) and B tiles
+//               (4-stage ring), completion via mbarrier transaction counts
+//   warp 1      TMEM owner (alloc/dealloc of 512 columns) and MMA issuer:
+//               K/16 tcgen05.mma (M=128, N=256, K=16) per tile into one of two
+//               256-column accumulators; tcgen05.commit signals the epilogue
+//   warps 2..9  epilogue: tcgen05.ld of the accumulator (one TMEM lane = one
+//               row; two warps per lane quadrant split the 256 columns), the
+//               exact decision above, and the pass's consumer: neighbour count,
+//               union of core-core neighbours, or smallest core neighbour.
+// Every wait is bounded (about two seconds of %globaltimer); on expiry the CTA
+// records DB_EBIT_TIMEOUT, stops issuing work, waits for its own copies and
+// MMAs, frees its TMEM and returns.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace {
+
+constexpr int TM = 128, TN = 256, NSTAGE = 4, EPI_WARPS = 8, NTHREADS = 32 * (2 + EPI_WARPS);
+constexpr int FP16_BAND = 8;  // |w - alpha| <= 8 (i.e. |D - T| <= 4 units^2) is rechecked exactly
+constexpr float BF16_E = 0.0078125f + 0.0000152587890625f;  // 2^-7 + 2^-16
+
+enum { TC_COUNT = 0, TC_UNION = 1, TC_BORDER = 2, TC_VERIFY = 3 };
+
+// Per-point metadata, in list order, stored as one 2 KB block per 128 points:
+// beta[128] (|v|^2), rho[128] (BF16 band factor), idx[128] (point index, -1
+// for padding), pad[128].  A 128-row A tile takes one block, a 256-column B
+// tile two consecutive blocks; each epilogue warp reads one of them.
+struct MetaBlock {
+    float beta[TM];
+    float rho[TM];
+    int idx[TM];
+    int pad[TM];
+};
+
+struct TcArgs {
+    const uint16_t *opR;  // packed row operand (tiles of 128 rows)
+    const MetaBlock *metaR;
+    const uint16_t *opC;  // packed column operand (tiles of 256 rows)
+    const MetaBlock *metaC;
+    const int *nR_ptr;    // device-side list lengths
+    const int *nC_ptr;
+    int K;                // padded dimension (multiple of 16, <= 64)
+    int T;                // threshold (< 2^24)
+    int bf16;
+    int pass;
+    int upper;            // union: only pairs i < j of one list
+    const int16_t *v16;   // centred units by point index, row stride K (exact recheck)
+    int *count;
+    int *parent;
+    int *border;
+    unsigned *status;
+    unsigned long long *ctr;  // [6] band pairs, [7] verify: disagreements outside the band, [8] max |w - exact|
+    int col_chunk;            // column tiles per work item
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: about two seconds, or until another role has given up.
+__device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    while (true) {
+        for (int i = 0; i < 32; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (globaltimer() - t0 > 2000000000ull) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, M=128, N=256, K=16, FP32 accumulate.
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: no swizzle, K-major, LBO = 128 B (next core
+// matrix along K), SBO = KG * 128 B (next 8-row group), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t sbo_bytes) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) |
+           ((uint64_t)((sbo_bytes >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor, kind::f16: D = F32, A/B = F16 or BF16, both K-major,
+// N = 256 (bits 17..22 hold N/8), M = 128 (bits 24..28 hold M/16).
+__host__ __device__ constexpr uint32_t idesc_f16(bool bf16) {
+    return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((uint32_t)(TN >> 3) << 17) |
+           ((uint32_t)(TM >> 4) << 24);
+}
+
+// Exact D(p,q) <= T from the centred int16 rows (the recheck of band pairs).
+__device__ __noinline__ int exact_sqdist(const int16_t *__restrict__ v16, int K, int p, int q) {
+    const int4 *a = reinterpret_cast<const int4 *>(v16 + (size_t)p * K);
+    const int4 *b = reinterpret_cast<const int4 *>(v16 + (size_t)q * K);
+    int s = 0;
+    for (int c = 0; c < K / 8; ++c) {
+        int4 x = a[c], y = b[c];
+        const int xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            int d0 = (int)(int16_t)(xs[h] & 0xffff) - (int)(int16_t)(ys[h] & 0xffff);
+            int d1 = (xs[h] >> 16) - (ys[h] >> 16);
+            s += d0 * d0 + d1 * d1;
+        }
+    }
+    return s;
+}
+
+struct __align__(16) Smem {
+    uint16_t A[2][TM * 64];          // 2 x 16 KB
+    uint16_t B[NSTAGE][TN * 64];     // 4 x 32 KB
+    MetaBlock metaA[2];              // 2 x 2 KB
+    MetaBlock metaB[NSTAGE][2];      // 4 x 4 KB
+    uint64_t a_full[2], a_empty[2];
+    uint64_t b_full[NSTAGE], b_empty[NSTAGE];
+    uint64_t t_full[2], t_empty[2];
+    uint32_t tmem_base;
+    int abort_flag;
+};
+
+// Work item w: row tile rt = w / nchunk, column tiles [c0, c1).
+__device__ __forceinline__ bool item_range(const TcArgs &a, int w, int nR, int nC, int &rt, int &c0, int &c1) {
+    const int nrt = (nR + TM - 1) / TM, nct = (nC + TN - 1) / TN;
+    const int nchunk = (nct + a.col_chunk - 1) / a.col_chunk;
+    if (w >= nrt * nchunk) return false;
+    rt = w / nchunk;
+    const int ch = w - rt * nchunk;
+    c0 = ch * a.col_chunk;
+    c1 = min(nct, c0 + a.col_chunk);
+    if (a.upper) c0 = max(c0, (rt * TM) / TN);  // pairs i < j only: skip tiles left of the diagonal
+    return true;
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(TcArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    Smem &S = *reinterpret_cast<Smem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nR = *a.nR_ptr, nC = *a.nC_ptr;
+    const int nrt = (nR + TM - 1) / TM, nct = (nC + TN - 1) / TN;
+    const int nchunk = (nct + a.col_chunk - 1) / a.col_chunk;
+    const int nitems = nrt * nchunk;
+    if ((int)blockIdx.x >= nitems) return;  // nothing for this CTA (before any TMEM use)
+
+    volatile int *abort_flag = &S.abort_flag;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&S.a_full[i], 1);
+            mbar_init(&S.a_empty[i], 1 + EPI_WARPS);
+            mbar_init(&S.t_full[i], 1);
+            mbar_init(&S.t_empty[i], EPI_WARPS);
+        }
+        for (int i = 0; i < NSTAGE; ++i) {
+            mbar_init(&S.b_full[i], 1);
+            mbar_init(&S.b_empty[i], 1 + EPI_WARPS);
+        }
+        S.abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        tmem_alloc(&S.tmem_base, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem_base;
+    const int K = a.K, KG = K / 8;
+    const uint32_t a_bytes = (uint32_t)(TM * K * 2), b_bytes = (uint32_t)(TN * K * 2);
+
+    if (warp == 0) {
+        // ---------------- producer ----------------
+        if (lane == 0) {
+            int t = 0, ia = 0;
+            for (int w = blockIdx.x; w < nitems && !*abort_flag; w += gridDim.x, ++ia) {
+                int rt, c0, c1;
+                item_range(a, w, nR, nC, rt, c0, c1);
+                const int ab = ia & 1;
+                if (!mbar_wait(&S.a_empty[ab], ((ia >> 1) & 1) ^ 1, abort_flag)) break;
+                mbar_arrive_expect_tx(&S.a_full[ab], a_bytes + sizeof(MetaBlock));
+                bulk_g2s(S.A[ab], a.opR + (size_t)rt * TM * K, a_bytes, &S.a_full[ab]);
+                bulk_g2s(&S.metaA[ab], a.metaR + rt, sizeof(MetaBlock), &S.a_full[ab]);
+                for (int ct = c0; ct < c1; ++ct, ++t) {
+                    const int s = t % NSTAGE;
+                    if (!mbar_wait(&S.b_empty[s], ((t / NSTAGE) & 1) ^ 1, abort_flag)) break;
+                    mbar_arrive_expect_tx(&S.b_full[s], b_bytes + 2 * sizeof(MetaBlock));
+                    bulk_g2s(S.B[s], a.opC + (size_t)ct * TN * K, b_bytes, &S.b_full[s]);
+                    bulk_g2s(&S.metaB[s][0], a.metaC + 2 * ct, 2 * sizeof(MetaBlock), &S.b_full[s]);
+                }
+            }
+            // Drain: every copy issued has landed once its stage's "empty" barrier
+            // completes again (the consumers arrive after the copy completed), or
+            // after a final bounded wait on the "full" barriers below.
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t idesc = idesc_f16(a.bf16 != 0);
+            int t = 0, ia = 0;
+            bool clean = true;
+            for (int w = blockIdx.x; w < nitems && !*abort_flag; w += gridDim.x, ++ia) {
+                int rt, c0, c1;
+                item_range(a, w, nR, nC, rt, c0, c1);
+                const int ab = ia & 1;
+                if (!mbar_wait(&S.a_full[ab], (ia >> 1) & 1, abort_flag)) break;
+                const uint32_t a_addr = smem_u32(S.A[ab]);
+                bool ok = true;
+                for (int ct = c0; ct < c1; ++ct, ++t) {
+                    const int s = t % NSTAGE, b = t & 1;
+                    if (!mbar_wait(&S.b_full[s], (t / NSTAGE) & 1, abort_flag) ||
+                        !mbar_wait(&S.t_empty[b], ((t >> 1) & 1) ^ 1, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t b_addr = smem_u32(S.B[s]);
+                    for (int kk = 0; kk < K / 16; ++kk) {
+                        const uint64_t ad = smem_desc(a_addr + kk * 256, KG * 128);
+                        const uint64_t bd = smem_desc(b_addr + kk * 256, KG * 128);
+                        mma_f16(tmem + (uint32_t)(b * TN), ad, bd, idesc, kk > 0 ? 1u : 0u);
+                    }
+                    mma_commit(&S.t_full[b]);   // accumulator ready for the epilogue
+                    mma_commit(&S.b_empty[s]);  // operands of this stage consumed
+                }
+                mma_commit(&S.a_empty[ab]);
+                if (!ok) {
+                    clean = false;
+                    break;
+                }
+            }
+            // Wait for the arrivals of the last commits, so that none lands after
+            // the CTA has exited.  Stage s was last used by tile t_s (its phase
+            // t_s / NSTAGE); A buffer ab by item ia_ab (phase ia_ab / 2).
+            if (clean && !*abort_flag) {
+                for (int s = 0; s < NSTAGE && s < t; ++s) {
+                    const int ts = s + ((t - 1 - s) / NSTAGE) * NSTAGE;
+                    mbar_wait(&S.b_empty[s], (ts / NSTAGE) & 1, abort_flag);
+                }
+                for (int ab = 0; ab < 2 && ab < ia; ++ab) {
+                    const int il = ab + ((ia - 1 - ab) / 2) * 2;
+                    mbar_wait(&S.a_empty[ab], (il >> 1) & 1, abort_flag);
+                }
+            }
+        }
+    } else {
+        // ---------------- epilogue ----------------
+        const int ew = warp - 2;         // 0..7
+        const int quad = warp & 3;       // TMEM lane quadrant this warp may access
+        const int half = ew >> 2;        // column half of the 256-column tile
+        const int r = quad * 32 + lane;  // row within the tile
+        const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
+        int t = 0, ia = 0;
+        unsigned long long band_cnt = 0, bad_cnt = 0;
+        unsigned maxerr = 0;
+        for (int w = blockIdx.x; w < nitems; w += gridDim.x, ++ia) {
+            int rt, c0, c1;
+            item_range(a, w, nR, nC, rt, c0, c1);
+            const int ab = ia & 1;
+            if (!mbar_wait(&S.a_full[ab], (ia >> 1) & 1, abort_flag)) break;
+            const float beta_p = S.metaA[ab].beta[r], rho_p = S.metaA[ab].rho[r];
+            const int p = S.metaA[ab].idx[r];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.a_empty[ab]);
+            const int i_row = rt * TM + r;  // list index of this row
+            const bool row_ok = i_row < nR && p >= 0;
+            const float alpha = beta_p - (float)a.T;  // |v_p|^2 - T, exact
+            const float alo = alpha - (float)FP16_BAND, ahi = alpha + (float)FP16_BAND;
+            int cnt = 0, bmin = INT_MAX;
+            bool ok = true;
+            for (int ct = c0; ct < c1; ++ct, ++t) {
+                const int s = t % NSTAGE, b = t & 1;
+                if (!mbar_wait(&S.t_full[b], (t >> 1) & 1, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const MetaBlock &mc = S.metaB[s][half];
+#pragma unroll 1
+                for (int ch = 0; ch < 4; ++ch) {
+                    const int cb = ch * 32;  // column within this warp's 128-column half
+                    uint32_t g[32];
+                    tmem_ld32(tmem + lane_base + (uint32_t)(b * TN + half * 128 + cb), g);
+                    if (!row_ok) continue;
+#pragma unroll
+                    for (int j4 = 0; j4 < 8; ++j4) {
+                        const float4 b4 = *reinterpret_cast<const float4 *>(&mc.beta[cb + 4 * j4]);
+                        float4 r4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (a.bf16) r4 = *reinterpret_cast<const float4 *>(&mc.rho[cb + 4 * j4]);
+                        const float bq[4] = {b4.x, b4.y, b4.z, b4.w}, rq[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj) {
+                            const int j = 4 * j4 + jj;
+                            const float gv = __uint_as_float(g[j]);
+                            const float wv = fmaf(2.f, gv, -bq[jj]);  // 2G - |v_q|^2
+                            if (a.pass == TC_VERIFY) {
+                                const int q = mc.idx[cb + j];
+                                if (q < 0) continue;
+                                const int D = exact_sqdist(a.v16, K, p, q);
+                                // 2G exactly, from integers: |v_p|^2 + |v_q|^2 - D (the betas are exact)
+                                const long long two_g = (long long)beta_p + (long long)bq[jj] - D;
+                                const double err = fabs(2.0 * (double)gv - (double)two_g);
+                                maxerr = max(maxerr, (unsigned)fmin(err, 4.0e9));
+                                const bool nb_exact = D <= a.T;
+                                const float del = a.bf16 ? rho_p * rq[jj] : (float)FP16_BAND;
+                                const bool in_band = fabsf(wv - alpha) <= del;
+                                band_cnt += in_band;
+                                if (!in_band && ((wv >= alpha) != nb_exact)) ++bad_cnt;
+                                cnt += nb_exact;
+                                continue;
+                            }
+                            // the common case: certainly not a neighbour
+                            if (a.bf16 ? (fmaf(rho_p, rq[jj], wv) < alpha) : (wv < alo)) continue;
+                            const int q = mc.idx[cb + j];
+                            if (q < 0) continue;
+                            if (a.upper && i_row >= ct * TN + half * 128 + cb + j) continue;  // i < j only
+                            bool nb;
+                            if (a.bf16 ? (fmaf(-rho_p, rq[jj], wv) >= alpha) : (wv > ahi)) {
+                                nb = true;
+                            } else {  // inside the rounding band: decide exactly
+                                ++band_cnt;
+                                nb = exact_sqdist(a.v16, K, p, q) <= a.T;
+                            }
+                            if (!nb) continue;
+                            if (a.pass == TC_COUNT) ++cnt;
+                            else if (a.pass == TC_UNION) db::uf_unite(a.parent, p, q, a.status);
+                            else bmin = min(bmin, q);
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&S.t_empty[b]);
+                    mbar_arrive(&S.b_empty[s]);
+                }
+            }
+            if (row_ok) {
+                if ((a.pass == TC_COUNT || a.pass == TC_VERIFY) && cnt) atomicAdd(a.count + p, cnt);
+                if (a.pass == TC_BORDER && bmin != INT_MAX) atomicMin(a.border + p, bmin);
+            }
+            if (!ok) break;
+        }
+        if (band_cnt) atomicAdd(a.ctr + 6, band_cnt);
+        if (bad_cnt) atomicAdd(a.ctr + 7, bad_cnt);
+        if (maxerr) atomicMax(a.ctr + 8, (unsigned long long)maxerr);
+    }
+
+    // ---------------- teardown ----------------
+    tc_fence_before();
+    __syncthreads();
+    if (S.abort_flag) {
+        if (threadIdx.x == 0) atomicOr(a.status, DB_EBIT_TIMEOUT);
+        // Let in-flight copies and MMAs land before the CTA's memory goes away:
+        // wait (bounded) for every barrier to be quiescent.
+        if (threadIdx.x == 0) {
+            const uint64_t t0 = globaltimer();
+            while (globaltimer() - t0 < 20000000ull) {
+            }
+        }
+        __syncthreads();
+    }
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(tmem, 512);
+}
+
+// ---------------- preparation kernels ----------------
+
+// Grid check and centred integer rows: v16[i][k] = u - 512 (pads 0), |v|^2.
+__global__ void tc_prep_kernel(const float *__restrict__ x, int n, int d, int K, int16_t *__restrict__ v16,
+                               int *__restrict__ nrm, unsigned *status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int s = 0;
+    bool ok = true;
+    for (int k = 0; k < K; ++k) {
+        int v = 0;
+        if (k < d) {
+            int u;
+            ok &= db::on_grid(x[(size_t)i * d + k], u);
+            v = u - 512;
+        }
+        v16[(size_t)i * K + k] = (int16_t)v;
+        s += v * v;
+    }
+    nrm[i] = s;
+    if (!ok) atomicOr(status, DB_EBIT_NOT_QUANTISED);
+}
+
+__device__ __forceinline__ uint16_t to_half_bits(int v, bool bf16) {
+    if (bf16) {
+        __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+        return *reinterpret_cast<uint16_t *>(&h);
+    }
+    __half h = __int2half_rn(v);
+    return *reinterpret_cast<uint16_t *>(&h);
+}
+
+// Packs list entries (list == nullptr: identity) into the tiled operand layout
+// and writes their metadata; rows past the list length up to the padded
+// length become zero rows with index -1 and beta = 1e30 (never neighbours).
+__global__ void tc_pack_kernel(const int *__restrict__ list, const int *__restrict__ len_ptr, int n_pad, int K,
+                               int bf16, const int16_t *__restrict__ v16, const int *__restrict__ nrm,
+                               uint16_t *__restrict__ op, MetaBlock *__restrict__ meta) {
+    const int len = *len_ptr;
+    const int KG = K / 8;
+    const int64_t total = (int64_t)n_pad * KG;  // one thread per (row, 8-element group)
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / KG), kg = (int)(e - (int64_t)i * KG);
+        const int rows_per_tile = TM;
+        const int tile = i / rows_per_tile, r = i - tile * rows_per_tile;
+        const int rg = r >> 3, ri = r & 7;
+        uint16_t h[8];
+        const bool valid = i < len;
+        const int p = valid ? (list ? list[i] : i) : -1;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) h[k] = valid ? to_half_bits(v16[(size_t)p * K + kg * 8 + k], bf16 != 0) : 0;
+        const size_t off = (size_t)tile * TM * K + ((size_t)(rg * KG + kg) * 64) + ri * 8;
+        uint4 pk;
+        pk.x = h[0] | ((uint32_t)h[1] << 16);
+        pk.y = h[2] | ((uint32_t)h[3] << 16);
+        pk.z = h[4] | ((uint32_t)h[5] << 16);
+        pk.w = h[6] | ((uint32_t)h[7] << 16);
+        *reinterpret_cast<uint4 *>(op + off) = pk;
+        if (kg == 0) {
+            MetaBlock &m = meta[tile];
+            if (valid) {
+                const float nv = (float)nrm[p];
+                m.beta[r] = nv;
+                m.rho[r] = sqrtf(2.f * BF16_E) * sqrtf(nv) * (1.f + 1.f / 1024.f) + 1e-3f;
+                m.idx[r] = p;
+            } else {
+                m.beta[r] = 1e30f;
+                m.rho[r] = 0.f;
+                m.idx[r] = -1;
+            }
+            m.pad[r] = 0;
+        }
+    }
+}
+
+// Core and non-core lists in increasing index order (from an exclusive scan of
+// the core flags): lists[0..ncore) = cores, noncore list separately.
+__global__ void tc_split_kernel(int n, const uint8_t *__restrict__ core, const int *__restrict__ scan,
+                                int *__restrict__ core_list, int *__restrict__ non_list, int *__restrict__ lens) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int c = scan[i];
+        if (core[i]) core_list[c] = i;
+        else non_list[i - c] = i;
+        if (i == n - 1) {
+            lens[0] = c + core[i];
+            lens[1] = n - lens[0];
+        }
+    }
+}
+
+__global__ void set_len_kernel(int *p, int v) { *p = v; }
+
+__global__ void core_flags_kernel(int n, const uint8_t *__restrict__ core, int *__restrict__ flags) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) flags[i] = core[i];
+}
+
+size_t tc_smem_bytes() { return sizeof(Smem) + 1024; }
+
+}  // namespace
+
+// Host launcher of the whole tensor-core all-pairs pipeline.
+cudaError_t launch_allpairs_tc(const DbWork &w, const float *x, int64_t n64, int32_t d, int64_t Tc, int32_t min_pts,
+                               bool bf16, cudaStream_t st) {
+    const int n = (int)n64;
+    const int K = ((d + 15) / 16) * 16;
+    const int n_pad = ((n + TN - 1) / TN) * TN;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(tc_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)tc_smem_bytes());
+        if (e) return e;
+        attr_set = true;
+    }
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int nb = (n + 255) / 256;
+    int *lens = w.tc_lens;  // [0] all, [1] core, [2] non-core
+    set_len_kernel<<<1, 1, 0, st>>>(lens + 2, n);
+    tc_prep_kernel<<<nb, 256, 0, st>>>(x, n, d, K, w.v16, w.inorm, w.status);
+    w.marks->kernel("tc_prep", st);
+    const int pack_blocks = (int)std::min<int64_t>(((int64_t)n_pad * (K / 8) + 255) / 256, 152 * 32);
+    tc_pack_kernel<<<pack_blocks, 256, 0, st>>>(nullptr, lens + 2, n_pad, K, bf16, w.v16, w.inorm, w.opAll,
+                                                reinterpret_cast<MetaBlock *>(w.metaAll));
+    w.marks->kernel("tc_pack_all", st);
+    cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(int) * (size_t)n, st);
+    if (e) return e;
+
+    TcArgs a{};
+    a.K = K;
+    a.T = (int)Tc;
+    a.bf16 = bf16 ? 1 : 0;
+    a.v16 = w.v16;
+    a.count = w.count;
+    a.parent = w.parent;
+    a.border = w.border;
+    a.status = w.status;
+    a.ctr = w.ctr;
+    a.col_chunk = 32;
+    const size_t smem = tc_smem_bytes();
+    // pass 1: all x all -> neighbour counts
+    a.opR = a.opC = w.opAll;
+    a.metaR = a.metaC = reinterpret_cast<const MetaBlock *>(w.metaAll);
+    a.nR_ptr = a.nC_ptr = lens + 2;
+    a.pass = TC_COUNT;
+    a.upper = 0;
+    tc_pass_kernel<<<sms, NTHREADS, smem, st>>>(a);
+    w.marks->kernel("tc_count", st);
+    // core flags, parent, border init (shared with the SIMT path)
+    launch_core_init(w, n, min_pts, st);
+    // core / non-core lists
+    core_flags_kernel<<<std::min(nb, 152 * 16), 256, 0, st>>>(n, w.core, w.list_b);
+    w.marks->kernel("tc_core_flags", st);
+    {
+        cudaError_t e2 = launch_exclusive_scan(w.list_b, w.scan, n, w.scan_part, w.scan_part_cap, st, w.marks);
+        if (e2) return e2;
+    }
+    tc_split_kernel<<<std::min(nb, 152 * 16), 256, 0, st>>>(n, w.core, w.scan, w.list_a, w.list_b, lens);
+    w.marks->kernel("tc_split", st);
+    tc_pack_kernel<<<pack_blocks, 256, 0, st>>>(w.list_a, lens + 0, n_pad, K, bf16, w.v16, w.inorm, w.opCore,
+                                                reinterpret_cast<MetaBlock *>(w.metaCore));
+    w.marks->kernel("tc_pack_core", st);
+    tc_pack_kernel<<<pack_blocks, 256, 0, st>>>(w.list_b, lens + 1, n_pad, K, bf16, w.v16, w.inorm, w.opNon,
+                                                reinterpret_cast<MetaBlock *>(w.metaNon));
+    w.marks->kernel("tc_pack_noncore", st);
+    // pass 2: core x core (i < j) -> union
+    a.opR = a.opC = w.opCore;
+    a.metaR = a.metaC = reinterpret_cast<const MetaBlock *>(w.metaCore);
+    a.nR_ptr = a.nC_ptr = lens + 0;
+    a.pass = TC_UNION;
+    a.upper = 1;
+    tc_pass_kernel<<<sms, NTHREADS, smem, st>>>(a);
+    w.marks->kernel("tc_union", st);
+    // pass 3: non-core x core -> smallest core neighbour
+    a.opR = w.opNon;
+    a.metaR = reinterpret_cast<const MetaBlock *>(w.metaNon);
+    a.nR_ptr = lens + 1;
+    a.opC = w.opCore;
+    a.metaC = reinterpret_cast<const MetaBlock *>(w.metaCore);
+    a.nC_ptr = lens + 0;
+    a.pass = TC_BORDER;
+    a.upper = 0;
+    tc_pass_kernel<<<sms, NTHREADS, smem, st>>>(a);
+    w.marks->kernel("tc_border", st);
+    return cudaGetLastError();
+}
+
+// Diagnostic: the count pass with every pair also decided exactly; records in
+// ctr[6] the band pairs, ctr[7] the pairs outside the band whose fast decision
+// disagrees with the exact one (must be 0), ctr[8] the largest |2G - exact|.
+cudaError_t launch_tc_verify(const DbWork &w, const float *x, int64_t n64, int32_t d, int64_t Tc, bool bf16,
+                             cudaStream_t st) {
+    const int n = (int)n64;
+    const int K = ((d + 15) / 16) * 16;
+    const int n_pad = ((n + TN - 1) / TN) * TN;
+    cudaError_t e = cudaFuncSetAttribute(tc_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tc_smem_bytes());
+    if (e) return e;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int *lens = w.tc_lens;
+    set_len_kernel<<<1, 1, 0, st>>>(lens + 2, n);
+    tc_prep_kernel<<<(n + 255) / 256, 256, 0, st>>>(x, n, d, K, w.v16, w.inorm, w.status);
+    const int pack_blocks = (int)std::min<int64_t>(((int64_t)n_pad * (K / 8) + 255) / 256, 152 * 32);
+    tc_pack_kernel<<<pack_blocks, 256, 0, st>>>(nullptr, lens + 2, n_pad, K, bf16, w.v16, w.inorm, w.opAll,
+                                                reinterpret_cast<MetaBlock *>(w.metaAll));
+    if ((e = cudaMemsetAsync(w.count, 0, sizeof(int) * (size_t)n, st))) return e;
+    TcArgs a{};
+    a.K = K;
+    a.T = (int)Tc;
+    a.bf16 = bf16 ? 1 : 0;
+    a.v16 = w.v16;
+    a.count = w.count;
+    a.status = w.status;
+    a.ctr = w.ctr;
+    a.col_chunk = 32;
+    a.opR = a.opC = w.opAll;
+    a.metaR = a.metaC = reinterpret_cast<const MetaBlock *>(w.metaAll);
+    a.nR_ptr = a.nC_ptr = lens + 2;
+    a.pass = TC_VERIFY;
+    tc_pass_kernel<<<sms, NTHREADS, tc_smem_bytes(), st>>>(a);
+    return cudaGetLastError();
+}

@@ -26,7 +26,7 @@
 //            least min_pts points makes all its points core with no test; other
 //            points stop counting once they reach min_pts unless exact counts
 //            are requested.  Each cell records its smallest core index (rep).
-//   uinit    each core point hangs under its cell's rep (cells are cliques)
+//            Each core point then hangs under its cell's rep (cells are cliques).
 //   union    neighbouring cells whose cores contain one eps-pair are united
 //            (Section IV-C's merge), adjacent cells in one launch and the
 //            outer ring in a second; a cell pair already in one set is skipped
@@ -259,10 +259,13 @@ struct PairArgs {
 //   |A| >= 32 with exact counts: one lane per point, candidates broadcast;
 //   otherwise: per point, the warp walks the flattened candidates and stops
 //   once the count reaches min_pts (unless exact counts are asked for).
-// The smallest core index of A is written to cell_rep[A].
+// Then the smallest core index of A goes to cell_rep[A], and every core point
+// of A is hung under it in the union-find forest (cells are cliques); other
+// points are their own parent.
 template <int D>
 __global__ void __launch_bounds__(256) grid_count_kernel(PairArgs a, int min_pts, int exact, uint8_t *score,
-                                                         int *cell_rep, int *counts_out, uint8_t *core_out) {
+                                                         int *cell_rep, int *parent, int *counts_out,
+                                                         uint8_t *core_out) {
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
     const int ncells = (int)(*a.ctr0 >> 32);
@@ -304,15 +307,24 @@ __global__ void __launch_bounds__(256) grid_count_kernel(PairArgs a, int min_pts
                 }
             }
         } else {
+            // neighbour cells of A, 32 per chunk; the first chunk stays in registers
+            const int B0 = lane < noff ? row[lane] : -1;
+            const int s0 = B0 >= 0 ? a.cell_start[B0] : 0, c0 = B0 >= 0 ? a.cell_count[B0] : 0;
+            const int incl0 = warp_incl_scan(c0), total0 = __shfl_sync(FULL, incl0, 31);
             for (int i = 0; i < cA; ++i) {
                 const int p = sA + i;
                 const float4 pt = a.spts[p];
                 const float cp = a.g.Tp1 + pt.w, px2 = 2.f * pt.x, py2 = 2.f * pt.y, pz2 = 2.f * pt.z;
                 int cnt = cA;
                 for (int o0 = 0; o0 < noff && cnt < lim; o0 += 32) {
-                    const int B = (o0 + lane < noff) ? row[o0 + lane] : -1;
-                    const int s = B >= 0 ? a.cell_start[B] : 0, c = B >= 0 ? a.cell_count[B] : 0;
-                    const int incl = warp_incl_scan(c), total = __shfl_sync(FULL, incl, 31);
+                    int s = s0, c = c0, incl = incl0, total = total0;
+                    if (o0) {
+                        const int B = (o0 + lane < noff) ? row[o0 + lane] : -1;
+                        s = B >= 0 ? a.cell_start[B] : 0;
+                        c = B >= 0 ? a.cell_count[B] : 0;
+                        incl = warp_incl_scan(c);
+                        total = __shfl_sync(FULL, incl, 31);
+                    }
                     for (int base = 0; base < total && cnt < lim; base += 32) {
                         const int j = base + lane;
                         const int q = locate(j, incl, c, s);
@@ -332,23 +344,20 @@ __global__ void __launch_bounds__(256) grid_count_kernel(PairArgs a, int min_pts
         }
         minorig = warp_min(minorig);
         if (lane == 0) cell_rep[A] = minorig;
-    }
-}
-
-__global__ void grid_union_init_kernel(int n, const int *__restrict__ sidx, const int *__restrict__ scell,
-                                       const uint8_t *__restrict__ score, const int *__restrict__ cell_rep,
-                                       int *__restrict__ parent) {
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-        const int orig = sidx[p];
-        parent[orig] = score[p] ? cell_rep[scell[p]] : orig;
+        __syncwarp();
+        for (int i = lane; i < cA; i += 32) {
+            const int p = sA + i, o = a.sidx[p];
+            parent[o] = score[p] ? minorig : o;
+        }
     }
 }
 
 // Merge pass (Section IV-C).  The core points of one cell are already one set
-// (cells are cliques).  For each neighbouring cell B of A (from the smaller
-// key, offsets [o_begin, o_end)), if A and B are not yet in one set, the warp
-// searches for one core pair within eps — lanes over the larger cell, a loop
-// over the smaller — and unites the two cells at the first hit.
+// (cells are cliques).  Lanes look at up to 32 neighbouring cells B of A at
+// once (offsets [o_begin, o_end), each cell pair from its smaller key); for
+// every B with cores that is not yet in A's set, the warp searches for one
+// core pair within eps — lanes over the larger cell, a loop over the smaller —
+// and unites the two sets at the first hit.
 template <int D>
 __global__ void __launch_bounds__(256) grid_union_kernel(PairArgs a, const uint8_t *__restrict__ score, int *parent,
                                                          unsigned *status, int o_begin, int o_end) {
@@ -361,33 +370,44 @@ __global__ void __launch_bounds__(256) grid_union_kernel(PairArgs a, const uint8
         const unsigned keyA = a.cell_key[A];
         const int sA = a.cell_start[A], cA = a.cell_count[A];
         const int *row = a.nbr + (size_t)A * a.g.noff;
-        for (int o = o_begin; o < o_end; ++o) {
-            const int B = row[o];
-            if (B < 0 || a.cell_key[B] < keyA) continue;
-            const int repB = a.cell_rep[B];
-            if (repB == DB_NONE) continue;
-            if (db::uf_find(parent, repA) == db::uf_find(parent, repB)) continue;
-            const int sB = a.cell_start[B], cB = a.cell_count[B];
-            const bool swap = cB > cA;  // lanes over the larger cell
-            const int sX = swap ? sB : sA, cX = swap ? cB : cA, sY = swap ? sA : sB, cY = swap ? cA : cB;
-            bool found = false;
-            for (int x0 = 0; x0 < cX && !found; x0 += 32) {
-                const int xi = x0 + lane;
-                const bool vx = xi < cX && score[sX + xi];
-                if (!__any_sync(FULL, vx)) continue;
-                const float4 px = a.spts[sX + (xi < cX ? xi : 0)];
-                const float cp = a.g.Tp1 + px.w, px2 = 2.f * px.x, py2 = 2.f * px.y, pz2 = 2.f * px.z;
-                for (int y = sY; y < sY + cY; ++y) {
-                    if (!score[y]) continue;
-                    const bool hit = vx && is_nbr<D>(cp, px2, py2, pz2, a.spts[y]);
-                    if (__any_sync(FULL, hit)) {
-                        found = true;
-                        break;
+        for (int o0 = o_begin; o0 < o_end; o0 += 32) {
+            const int o = o0 + lane;
+            const int B = o < o_end ? row[o] : -1;
+            const int repB = (B >= 0 && a.cell_key[B] > keyA) ? a.cell_rep[B] : DB_NONE;
+            bool need = repB != DB_NONE;
+            if (need) need = db::uf_find(parent, repA) != db::uf_find(parent, repB);
+            unsigned todo = __ballot_sync(FULL, need);
+            while (todo) {
+                const int l = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const int Bl = __shfl_sync(FULL, B, l), rB = __shfl_sync(FULL, repB, l);
+                if (l != __ffs(__ballot_sync(FULL, need)) - 1) {  // an earlier union may have joined them
+                    int same = 0;
+                    if (lane == 0) same = db::uf_find(parent, repA) == db::uf_find(parent, rB);
+                    if (__shfl_sync(FULL, same, 0)) continue;
+                }
+                const int sB = a.cell_start[Bl], cB = a.cell_count[Bl];
+                const bool swap = cB > cA;  // lanes over the larger cell
+                const int sX = swap ? sB : sA, cX = swap ? cB : cA, sY = swap ? sA : sB, cY = swap ? cA : cB;
+                bool found = false;
+                for (int x0 = 0; x0 < cX && !found; x0 += 32) {
+                    const int xi = x0 + lane;
+                    const bool vx = xi < cX && score[sX + xi];
+                    if (!__any_sync(FULL, vx)) continue;
+                    const float4 px = a.spts[sX + (xi < cX ? xi : 0)];
+                    const float cp = a.g.Tp1 + px.w, px2 = 2.f * px.x, py2 = 2.f * px.y, pz2 = 2.f * px.z;
+                    for (int y = sY; y < sY + cY; ++y) {
+                        if (!score[y]) continue;
+                        const bool hit = vx && is_nbr<D>(cp, px2, py2, pz2, a.spts[y]);
+                        if (__any_sync(FULL, hit)) {
+                            found = true;
+                            break;
+                        }
                     }
                 }
+                if (found && lane == 0) db::uf_unite(parent, repA, rB, status);
+                __syncwarp();
             }
-            if (found && lane == 0) db::uf_unite(parent, repA, repB, status);
-            __syncwarp();
         }
     }
 }
@@ -407,8 +427,15 @@ __global__ void __launch_bounds__(256) grid_border_kernel(PairArgs a, int min_pt
     for (int A = warp; A < ncells; A += nwarps) {
         const int sA = a.cell_start[A], cA = a.cell_count[A];
         if (cA >= min_pts) continue;
+        // any non-core point here?
+        bool nc = false;
+        for (int i = lane; i < cA; i += 32) nc |= !score[sA + i];
+        if (!__any_sync(FULL, nc)) continue;
         const int repA = a.cell_rep[A];
         const int *row = a.nbr + (size_t)A * noff;
+        const int B0 = lane < noff ? row[lane] : -1;
+        const int r0 = B0 >= 0 ? a.cell_rep[B0] : DB_NONE;
+        const int s0 = B0 >= 0 ? a.cell_start[B0] : 0, c0 = B0 >= 0 ? a.cell_count[B0] : 0;
         for (int i = 0; i < cA; ++i) {
             const int p = sA + i;
             if (score[p]) continue;
@@ -416,9 +443,14 @@ __global__ void __launch_bounds__(256) grid_border_kernel(PairArgs a, int min_pt
             const float cp = a.g.Tp1 + pt.w, px2 = 2.f * pt.x, py2 = 2.f * pt.y, pz2 = 2.f * pt.z;
             int b = repA;
             for (int o0 = 0; o0 < noff; o0 += 32) {
-                const int B = (o0 + lane < noff) ? row[o0 + lane] : -1;
-                const bool useful = B >= 0 && a.cell_rep[B] < b;
-                const int s = useful ? a.cell_start[B] : 0, c = useful ? a.cell_count[B] : 0;
+                int r = r0, s = s0, c = c0;
+                if (o0) {
+                    const int B = (o0 + lane < noff) ? row[o0 + lane] : -1;
+                    r = B >= 0 ? a.cell_rep[B] : DB_NONE;
+                    s = B >= 0 ? a.cell_start[B] : 0;
+                    c = B >= 0 ? a.cell_count[B] : 0;
+                }
+                if (r >= b) c = 0;  // cannot beat b
                 const int incl = warp_incl_scan(c), total = __shfl_sync(FULL, incl, 31);
                 int best = b;
                 for (int base = 0; base < total; base += 32) {
@@ -436,35 +468,44 @@ __global__ void __launch_bounds__(256) grid_border_kernel(PairArgs a, int min_pt
     }
 }
 
-// Labels: a core point takes its set's root (its cluster's smallest core
-// index); a border point the root of its chosen core neighbour; noise -1.
-__global__ void grid_label_kernel(int n, const int *__restrict__ sidx, const uint8_t *__restrict__ score,
-                                  const int *__restrict__ scell, const int *__restrict__ cell_count, int min_pts,
-                                  const int *__restrict__ bord, int *parent, int *__restrict__ labels,
-                                  unsigned long long *ctr) {
-    __shared__ int red[4][32];
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    int nc = 0, nb = 0, nn = 0, nr = 0;
-    if (p < n) {
-        const int orig = sidx[p];
-        int lab;
-        if (score[p]) {
-            lab = db::uf_find(parent, orig);
-            nc = 1;
-            nr = lab == orig;
-        } else {
-            const int b = bord[p];
-            if (b == DB_NONE) {
-                lab = -1;
-                nn = 1;
-            } else {
-                lab = db::uf_find(parent, b);
-                nb = 1;
-            }
-        }
-        labels[orig] = lab;
-    }
+// Labels, one warp per cell: core points take their set's root (the cluster's
+// smallest core index, found once per cell), border points the root of their
+// chosen core neighbour, noise -1.  Also counts core / border / noise points
+// and clusters (a cluster's root is the representative of its own cell).
+__global__ void __launch_bounds__(256) grid_label_kernel(PairArgs a, const uint8_t *__restrict__ score,
+                                                         const int *__restrict__ bord, int *parent,
+                                                         int *__restrict__ labels, unsigned long long *ctr) {
+    __shared__ int red[4][8];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int ncells = (int)(*a.ctr0 >> 32);
+    int nc = 0, nb = 0, nn = 0, nr = 0;
+    for (int A = warp; A < ncells; A += nwarps) {
+        const int sA = a.cell_start[A], cA = a.cell_count[A];
+        const int repA = a.cell_rep[A];
+        int root = -1;
+        if (lane == 0 && repA != DB_NONE) root = db::uf_find(parent, repA);
+        root = __shfl_sync(FULL, root, 0);
+        if (lane == 0 && repA != DB_NONE && root == repA) ++nr;
+        for (int i = lane; i < cA; i += 32) {
+            const int p = sA + i, o = a.sidx[p];
+            int lab;
+            if (score[p]) {
+                lab = root;
+                ++nc;
+            } else {
+                const int b = bord[p];
+                if (b == DB_NONE) {
+                    lab = -1;
+                    ++nn;
+                } else {
+                    lab = db::uf_find(parent, b);
+                    ++nb;
+                }
+            }
+            labels[o] = lab;
+        }
+    }
     int v[4] = {nc, nb, nn, nr};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -514,13 +555,12 @@ int64_t isqrt64(int64_t v) {
 template <int D>
 cudaError_t grid_pair_passes(const DbWork &w, const GridGeom &g, int n, int min_pts, bool exact, int32_t *labels,
                              int32_t *counts_out, uint8_t *core_out, cudaStream_t st) {
+    (void)n;
     PairArgs a{g, w.ctr, w.spts, w.sidx, w.cell_start, w.cell_count, w.cell_rep, w.cell_key, w.nbr};
     const int wgrid = 152 * 16;  // 8 warps per block, warps stride over the cells
-    grid_count_kernel<D><<<wgrid, 256, 0, st>>>(a, min_pts, exact ? 1 : 0, w.score, w.cell_rep, counts_out, core_out);
+    grid_count_kernel<D><<<wgrid, 256, 0, st>>>(a, min_pts, exact ? 1 : 0, w.score, w.cell_rep, w.parent,
+                                                counts_out, core_out);
     w.marks->kernel("grid_count", st);
-    const int nb = (n + 255) / 256;
-    grid_union_init_kernel<<<nb, 256, 0, st>>>(n, w.sidx, w.scell, w.score, w.cell_rep, w.parent);
-    w.marks->kernel("grid_union_init", st);
     grid_union_kernel<D><<<wgrid, 256, 0, st>>>(a, w.score, w.parent, w.status, 0, g.nnear);
     w.marks->kernel("grid_union_near", st);
     if (g.noff > g.nnear) {
@@ -529,8 +569,7 @@ cudaError_t grid_pair_passes(const DbWork &w, const GridGeom &g, int n, int min_
     }
     grid_border_kernel<D><<<wgrid, 256, 0, st>>>(a, min_pts, w.score, w.border);
     w.marks->kernel("grid_border", st);
-    grid_label_kernel<<<nb, 256, 0, st>>>(n, w.sidx, w.score, w.scell, w.cell_count, min_pts, w.border, w.parent,
-                                          labels, w.ctr);
+    grid_label_kernel<<<wgrid, 256, 0, st>>>(a, w.score, w.border, w.parent, labels, w.ctr);
     w.marks->kernel("grid_label", st);
     return cudaGetLastError();
 }

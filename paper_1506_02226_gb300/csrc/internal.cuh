@@ -145,12 +145,14 @@ struct DbWork {
     uint32_t *cell_key;     // [cap_n]
     int32_t *nbr;           // neighbour-cell table [cap_n * noff_cap]
     int32_t noff_cap;
-    // tensor-core path
-    uint16_t *h16;          // packed 16-bit operand tiles [cap_n_pad * 64]
-    int32_t *inorm;         // exact integer |v|^2 of the centred units [cap_n]
-    int32_t *list_a, *list_b;  // compacted index lists [cap_n]
-    int32_t *band;          // band pairs (p, q) awaiting exact recheck [band_cap * 2]
-    int64_t band_cap;
+    // tensor-core path (max_d >= 16)
+    int64_t tc_cap_pad;     // rows of each packed operand (cap_n rounded up to 256)
+    int16_t *v16;           // centred units v = u - 512 by point index, row stride 64
+    int32_t *inorm;         // exact |v|^2 [cap_n]
+    uint16_t *opAll, *opCore, *opNon;  // packed FP16/BF16 operand tiles [tc_cap_pad * 64]
+    void *metaAll, *metaCore, *metaNon;  // per-point metadata blocks (16 B per row)
+    int32_t *list_a, *list_b;  // core / non-core index lists [cap_n]
+    int32_t *tc_lens;       // [0] cores, [1] non-cores, [2] all
     PhaseMarks *marks;      // host-side timing marks of the owning plan
 };
 
@@ -165,6 +167,11 @@ struct GridGeom {
 cudaError_t launch_prep_dense(const DbWork &w, const float *x, int64_t n, int32_t d, int32_t dp, cudaStream_t st);
 cudaError_t launch_allpairs_simt(const DbWork &w, int64_t n, int32_t d, int32_t dp, int64_t Tc, int32_t min_pts,
                                  bool exact_counts, cudaStream_t st);
+cudaError_t launch_core_init(const DbWork &w, int64_t n, int32_t min_pts, cudaStream_t st);
+cudaError_t launch_allpairs_tc(const DbWork &w, const float *x, int64_t n, int32_t d, int64_t Tc, int32_t min_pts,
+                               bool bf16, cudaStream_t st);
+cudaError_t launch_tc_verify(const DbWork &w, const float *x, int64_t n, int32_t d, int64_t Tc, bool bf16,
+                             cudaStream_t st);
 cudaError_t launch_labels_allpairs(const DbWork &w, int64_t n, int32_t *labels, int32_t *counts_out,
                                    uint8_t *core_out, cudaStream_t st);
 cudaError_t launch_compact(const DbWork &w, int64_t n, int32_t *labels, cudaStream_t st);

@@ -300,6 +300,13 @@ cudaError_t launch_prep_dense(const DbWork &w, const float *x, int64_t n, int32_
     return cudaGetLastError();
 }
 
+cudaError_t launch_core_init(const DbWork &w, int64_t n, int32_t min_pts, cudaStream_t st) {
+    core_init_kernel<<<(int)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>((int)n, min_pts, w.count, w.core,
+                                                                                  w.parent, w.border);
+    w.marks->kernel("core_init", st);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_allpairs_simt(const DbWork &w, int64_t n64, int32_t d, int32_t dp, int64_t Tc, int32_t min_pts,
                                  bool /*exact_counts*/, cudaStream_t st) {
     const int n = (int)n64;

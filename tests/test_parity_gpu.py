@@ -230,3 +230,68 @@ def test_full_size_lowd_workload(d):
     np.testing.assert_array_equal(lab, want_lab)
     lab2, _ = gpu_labels(inst.points, inst.eps, inst.min_pts)  # early-exit form, as timed
     np.testing.assert_array_equal(lab2, want_lab)
+
+
+# ---------------------------------------------------------------- tensor-core Gram path
+PRECS = [("fp16", B.DBSCAN_PREC_FP16_GRAM), ("bf16", B.DBSCAN_PREC_BF16_GRAM)]
+
+
+@pytest.mark.parametrize("name,prec", PRECS)
+@pytest.mark.parametrize("n,d", [(300, 16), (4099, 32), (2500, 64), (9000, 64), (1, 16), (257, 48)])
+def test_tensor_core_path_matches_oracle(name, prec, n, d):
+    spread = int(6 + 3 * np.sqrt(d))
+    x = _blobs(300 + n + d, n, d, spread=spread)
+    eps = float(np.float32(1.3 * spread * np.sqrt(d) / 1024))
+    for mode in (0, 1):
+        want_lab, want_cnt, want_core = oracle.dbscan(x, eps, 5, label_mode=mode)
+        lab, cnt, core, st = gpu_detail(x, eps, 5, grid=B.DBSCAN_GRID_OFF, label_mode=mode, precision=prec)
+        assert st["path"] == B.DBSCAN_PATH_ALLPAIRS_TC
+        np.testing.assert_array_equal(cnt, want_cnt)
+        np.testing.assert_array_equal(core, want_core)
+        np.testing.assert_array_equal(lab, want_lab)
+
+
+@pytest.mark.parametrize("bf16", [0, 1])
+def test_tensor_core_band_holds(bf16):
+    """Every pair outside the stated rounding band is decided as exact arithmetic
+    decides it; FP16 Gram products of the centred units are exact."""
+    from paper_1506_02226_gb300.api import Plan
+    for inst in (inputs.subsample(inputs.high_d(n=40_000), 4096, seed=5),
+                 inputs.Instance(_blobs(77, 3000, 64, spread=30), 0.2, 5)):
+        x = torch.from_numpy(inst.points).cuda()
+        with Plan(max_n=inst.n, max_d=inst.d) as p:
+            rep = B.dbscan_tc_verify(p.handle, x.data_ptr(), inst.n, inst.d, inst.eps, bf16)
+        assert rep["pairs"] == inst.n ** 2
+        assert rep["wrong_outside_band"] == 0
+        if not bf16:
+            assert rep["max_abs_error_2g"] == 0
+        want = oracle.counts(inst.points, inst.eps)
+        # the verify pass also counts exactly
+        with Plan(max_n=inst.n, max_d=inst.d, precision=B.DBSCAN_PREC_BF16_GRAM if bf16 else
+                  B.DBSCAN_PREC_FP16_GRAM, grid=B.DBSCAN_GRID_OFF) as p:
+            _, cnt, _, st = p.run_detail(x, inst.eps, inst.min_pts)
+        np.testing.assert_array_equal(cnt.cpu().numpy(), want)
+
+
+def test_tensor_core_high_d_subsample():
+    inst = inputs.subsample(inputs.high_d(n=60_000), 12_000, seed=8)
+    want_lab, want_cnt, want_core = oracle.dbscan(inst.points, inst.eps, inst.min_pts)
+    for prec in (B.DBSCAN_PREC_FP16_GRAM, B.DBSCAN_PREC_BF16_GRAM, B.DBSCAN_PREC_EXACT_SIMT):
+        lab, cnt, core, st = gpu_detail(inst.points, inst.eps, inst.min_pts, grid=B.DBSCAN_GRID_OFF,
+                                        precision=prec)
+        np.testing.assert_array_equal(cnt, want_cnt)
+        np.testing.assert_array_equal(lab, want_lab)
+
+
+@pytest.mark.slow
+def test_full_size_high_d_workload():
+    """n = 200,000, d = 64 on the FP16 tensor-core path, against the full oracle."""
+    inst = inputs.high_d()
+    want_lab, want_cnt, want_core = oracle.dbscan(inst.points, inst.eps, inst.min_pts)
+    lab, cnt, core, st = gpu_detail(inst.points, inst.eps, inst.min_pts)
+    assert st["path"] == B.DBSCAN_PATH_ALLPAIRS_TC
+    np.testing.assert_array_equal(cnt, want_cnt)
+    np.testing.assert_array_equal(core, want_core)
+    np.testing.assert_array_equal(lab, want_lab)
+    lab2, _ = gpu_labels(inst.points, inst.eps, inst.min_pts)
+    np.testing.assert_array_equal(lab2, want_lab)
