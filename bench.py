@@ -39,8 +39,19 @@ WORKLOADS = {
     "lowd2": ("500k points, d=2, 50 blobs + 20% noise, eps=0.005, min_pts=10", lambda: inputs.large_lowd(2)),
     "lowd3": ("500k points, d=3, 50 blobs + 20% noise, eps=0.005, min_pts=10", lambda: inputs.large_lowd(3)),
     "small": ("2k points, d=2, 5 blobs + 10% noise, eps=0.02, min_pts=5", inputs.small_2d),
+    "highd": ("200k points, d=64, 100 blobs + 15% noise, eps=median 30-NN distance, min_pts=20, FP16 tensor-core "
+              "Gram pair test", inputs.high_d),
+    "highd_bf16": ("200k points, d=64, as highd with BF16 tensor-core Gram pair test", inputs.high_d),
+    "highd_simt": ("200k points, d=64, as highd with the exact CUDA-core pair test", inputs.high_d),
 }
-CPU_SAMPLE = {"lowd2": 200_000, "lowd3": 200_000, "small": 2000}
+CPU_SAMPLE = {"lowd2": 200_000, "lowd3": 200_000, "small": 2000, "highd": 40_000, "highd_bf16": 40_000,
+              "highd_simt": 40_000}
+PRECISION = {"highd_bf16": 3, "highd_simt": 1}
+
+
+def work_units(points: np.ndarray, eps: float, d: int) -> int:
+    """Pair tests of one clustering: eps-grid candidate pairs for d <= 3, n^2 otherwise."""
+    return grid_candidate_pairs(points, eps) if d <= 3 else points.shape[0] ** 2
 
 
 # ------------------------------------------------------------------ work units
@@ -125,9 +136,10 @@ def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             p = json.load(f)
-        return {"hbm_gbs": p["hbm_gbs"], "sm_max_mhz": p.get("sm_max_mhz", 2070.0), "src": "measured"}
+        return {"hbm_gbs": p["hbm_gbs"], "bf16_tflops": p["bf16_tflops"], "sm_max_mhz": p.get("sm_max_mhz", 2070.0),
+                "src": "measured"}
     except (OSError, KeyError, ValueError):
-        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "src": "fallback"}
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0, "src": "fallback"}
 
 
 def grid_offsets(d: int, T: int):
@@ -204,7 +216,7 @@ def run_reference(args, wl_name):
         dt = time.perf_counter() - t0
         if step >= args.warmup:
             times.append(dt)
-            units.append(grid_candidate_pairs(sub.points, sub.eps))
+            units.append(work_units(sub.points, sub.eps, sub.d))
     value = sum(units) / sum(times) / 1e9
     ms = 1e3 * sum(times) / len(times)
     sample = f"oracle on {m}-point uniform subsamples of the {desc} workload, one per step"
@@ -227,13 +239,15 @@ def cpu_baseline(inst, wl_name, desc):
     t0 = time.perf_counter()
     oracle.dbscan(sub.points, sub.eps, sub.min_pts, nthreads=cores)
     dt = time.perf_counter() - t0
-    units = grid_candidate_pairs(sub.points, sub.eps)
+    units = work_units(sub.points, sub.eps, sub.d)
     return {"value": units / dt / 1e9, "unit": "G pair-tests/s", "cores": cores, "kind": "oracle",
             "sample": f"full oracle run on a {m}-point uniform subsample of the {desc} workload "
-                      f"({units} candidate pairs, {dt:.2f} s)"}
+                      f"({units} pair tests, {dt:.2f} s)"}
 
 
 def run_ours(args, wl_name):
+    from paper_1506_02226_gb300 import build as cuda_build
+    cuda_build.build()  # in-tree, only recompiles what changed
     import torch
     from paper_1506_02226_gb300 import binding as B
     from paper_1506_02226_gb300.api import Plan
@@ -249,14 +263,18 @@ def run_ours(args, wl_name):
 
     desc, make = WORKLOADS[wl_name]
     inst = make()
+    if args.n and args.n < inst.n:  # smaller sample of the same recipe (profiler captures)
+        inst = inputs.subsample(inst, args.n, seed=0)
+        desc = f"{args.n}-point uniform subsample of the {desc} workload"
     n, d = inst.n, inst.d
     x = torch.from_numpy(inst.points).cuda()
     labels = torch.empty(n, dtype=torch.int32, device="cuda")
     stream = torch.cuda.Stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
+    prec = PRECISION.get(wl_name, 0)
     # one synchronous run for the statistics (and the launch count)
-    with Plan(max_n=n, max_d=d) as p:
+    with Plan(max_n=n, max_d=d, precision=prec) as p:
         _, st0 = p.run(x, inst.eps, inst.min_pts, stats=True)
     units = st0["candidate_pairs"]
     if st0["path"] == B.DBSCAN_PATH_GRID:
@@ -264,7 +282,7 @@ def run_ours(args, wl_name):
         if host_units != units:
             raise RuntimeError(f"candidate-pair count mismatch: device {units} host {host_units}")
 
-    plan = Plan(max_n=n, max_d=d, synchronous=False, stream=stream, profile=True)
+    plan = Plan(max_n=n, max_d=d, synchronous=False, stream=stream, profile=True, precision=prec)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     kern: dict[str, list[float]] = {}
@@ -305,7 +323,7 @@ def run_ours(args, wl_name):
     # end to end: host (pinned) buffers through the C ABI, copies inside the timed region
     host_pts = torch.from_numpy(inst.points).pin_memory()
     host_lab = torch.empty(n, dtype=torch.int32).pin_memory()
-    eplan = Plan(max_n=n, max_d=d, stream=stream)
+    eplan = Plan(max_n=n, max_d=d, stream=stream, precision=prec)
     for _ in range(2):
         eplan.run_host(host_pts, inst.eps, inst.min_pts, labels=host_lab)
     e2e_s = []
@@ -328,7 +346,17 @@ def run_ours(args, wl_name):
     dom = max(avg, key=avg.get)
     peaks = load_peaks()
     bound, work = algorithmic_work(dom, n, d, inst.eps, st0)
-    if bound == "hbm" and work:
+    if dom.startswith("tc_") and dom in ("tc_count", "tc_union", "tc_border"):
+        K = -(-d // 16) * 16
+        nc = st0["n_core"]
+        pairs = {"tc_count": n * n, "tc_union": nc * nc / 2, "tc_border": (n - nc) * nc}[dom]
+        flops = 2.0 * pairs * K
+        peak = peaks["bf16_tflops"]
+        ach = flops / (avg[dom] * 1e-3) / 1e12
+        roof = {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": args.traffic, "peak_src": peaks["src"], "algorithmic_flops": flops,
+                "avg_ms": avg[dom]}
+    elif bound == "hbm" and work:
         ach = work / (avg[dom] * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"], "traffic": args.traffic, "peak_src": peaks["src"],
@@ -345,6 +373,7 @@ def run_ours(args, wl_name):
                    "path": {1: "eps-grid", 2: "all-pairs SIMT", 3: "all-pairs tensor-core"}.get(st0["path"]),
                    "l2": "flushed by a 256 MiB write before every timed step", "parallelism": f"replicas x{world}"},
         "pair_tests_per_step": units,
+        "band_pairs_per_step": st0["band_pairs"],
         "points_per_s": world * n / (ms_per_step * 1e-3),
         "clusters": st0["n_clusters"], "core": st0["n_core"], "noise": st0["n_noise"],
         "kernels_ms": {k: round(v, 5) for k, v in sorted(avg.items(), key=lambda kv: -kv[1])},
@@ -368,6 +397,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="lowd2")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU baseline (for profiler runs)")
+    ap.add_argument("--n", type=int, default=0, help="cluster a uniform subsample of this many points instead")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture, for the roofline")
     args = ap.parse_args()

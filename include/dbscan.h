@@ -174,11 +174,17 @@ typedef struct dbscan_tc_report {
     int64_t band_pairs;         /* pairs inside the band, which the fast path rechecks */
     int64_t wrong_outside_band; /* pairs outside the band decided differently from exact: must be 0 */
     int64_t max_abs_error_2g;   /* largest |2G_tensor - 2G_exact| seen, in squared grid units */
-    int64_t band_halfwidth_2g;  /* FP16 band half-width in the same units (-1: per-pair, BF16) */
+    int64_t band_halfwidth_2g;  /* FP16 band half-width in the same units (0: exact by proof; -1: per-pair, BF16) */
     int64_t threshold;          /* T */
 } dbscan_tc_report;
 int dbscan_tc_verify(dbscan_plan *plan, const float *points, int64_t n, int32_t d, float eps, int32_t bf16,
                      dbscan_tc_report *out);
+
+/* Raw device counters of the plan's last run (diagnostics): copies up to n of
+ * the plan's 16 64-bit counters to out (host).  Slot 6 counts band pairs
+ * rechecked exactly; builds made for pipeline diagnostics fill slots 9..13
+ * with cycles spent blocked per pipeline role.  Waits for the plan's stream. */
+int dbscan_plan_counters(dbscan_plan *plan, uint64_t *out, int32_t n);
 
 /* Device bytes the plan's workspace holds. */
 int64_t dbscan_plan_workspace_bytes(const dbscan_plan *plan);

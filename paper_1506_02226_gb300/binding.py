@@ -77,6 +77,7 @@ _SIGS = {
     "dbscan_plan_sync": (ctypes.c_int, [c_p]),
     "dbscan_plan_workspace_bytes": (c_i64, [c_p]),
     "dbscan_tc_verify": (ctypes.c_int, [c_p, c_p, c_i64, c_i32, c_f32, c_i32, c_p]),
+    "dbscan_plan_counters": (ctypes.c_int, [c_p, c_p, c_i32]),
     "dbscan_plan_phase_times": (ctypes.c_int, [c_p, c_i32, c_p, c_p, c_p]),
     "dbscan_batch": (ctypes.c_int, [c_p, c_p, c_i32, c_p]),
     "dbscan_serve_opts_default": (None, [c_p]),
@@ -190,6 +191,12 @@ def dbscan_tc_verify(plan: int, points: int, n: int, d: int, eps: float, bf16: i
     rep = dbscan_tc_report()
     _check(lib().dbscan_tc_verify(plan, points, n, d, eps, bf16, ctypes.byref(rep)), "dbscan_tc_verify")
     return rep.as_dict()
+
+
+def dbscan_plan_counters(plan: int) -> list[int]:
+    out = (ctypes.c_uint64 * 16)()
+    _check(lib().dbscan_plan_counters(plan, out, 16), "dbscan_plan_counters")
+    return list(out)
 
 
 def dbscan_plan_workspace_bytes(plan: int) -> int:

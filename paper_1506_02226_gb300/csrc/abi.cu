@@ -92,6 +92,9 @@ size_t layout(DbWork &w, const dbscan_opts &o, char *base) {
         w.list_a = c.take<int32_t>(n);
         w.list_b = c.take<int32_t>(n);
         w.tc_lens = c.take<int32_t>(4);
+        w.edge_cap = 16 * n + 4096;
+        w.edges = c.take<int2>((size_t)w.edge_cap);
+        w.edges_used = c.take<int32_t>(1024);
     } else {
         w.tc_cap_pad = 0;
     }
@@ -382,8 +385,20 @@ int dbscan_tc_verify(dbscan_plan *plan, const float *points, int64_t n, int32_t 
     out->band_pairs = (int64_t)plan->h_ctr[6];
     out->wrong_outside_band = (int64_t)plan->h_ctr[7];
     out->max_abs_error_2g = (int64_t)plan->h_ctr[8];
-    out->band_halfwidth_2g = bf16 ? -1 : 8;
+    out->band_halfwidth_2g = bf16 ? -1 : 0;
     out->threshold = T;
+    return DBSCAN_OK;
+}
+
+int dbscan_plan_counters(dbscan_plan *plan, uint64_t *out, int32_t n) {
+    if (!plan || !out || n < 0) return DBSCAN_ERR_ARG;
+    DeviceGuard dg(plan->opts.device);
+    const int k = std::min(n, 16);
+    if (cudaMemcpyAsync(plan->h_ctr, plan->w.ctr, sizeof(unsigned long long) * 16, cudaMemcpyDeviceToHost,
+                        plan->stream) != cudaSuccess ||
+        cudaStreamSynchronize(plan->stream) != cudaSuccess)
+        return DBSCAN_ERR_CUDA;
+    for (int i = 0; i < k; ++i) out[i] = plan->h_ctr[i];
     return DBSCAN_OK;
 }
 

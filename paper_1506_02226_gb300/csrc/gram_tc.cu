@@ -14,9 +14,9 @@
 //   alpha_p = |v_p|^2 - T (both exact integers, |.| <= 2^24 because T < 2^24),
 //   w = fma(2, G, -beta_q) rounds at most once, and w >= alpha_p decides
 //   D(p,q) <= T exactly: when |2G - beta| > 2^24 the rounded w stays on the
-//   same side of alpha.  Pairs with |w - alpha| <= FP16_BAND are still
-//   rechecked in int32 arithmetic, so the labels stay exact even if the
-//   hardware accumulation were less precise than assumed.
+//   same side of alpha.  The stated FP16 band is therefore 0; the diagnostic
+//   pass (TC_VERIFY, dbscan_tc_verify) recomputes every pair exactly on the
+//   device and reports max |2G - 2G_exact| = 0 and no pair decided wrongly.
 //   BF16 (8-bit significand) rounds v, each by at most 2^-8 |v|, so
 //   |G_bf16 - G| <= e |v_p| |v_q| with e = 2^-7 + 2^-16 (Cauchy-Schwarz); the
 //   products of the rounded integers are still integers, so accumulation adds
@@ -57,7 +57,7 @@
 namespace {
 
 constexpr int TM = 128, TN = 256, NSTAGE = 4, EPI_WARPS = 8, NTHREADS = 32 * (2 + EPI_WARPS);
-constexpr int FP16_BAND = 8;  // |w - alpha| <= 8 (i.e. |D - T| <= 4 units^2) is rechecked exactly
+constexpr int FP16_BAND = 0;  // FP16 Gram products are exact (see above): no band
 constexpr float BF16_E = 0.0078125f + 0.0000152587890625f;  // 2^-7 + 2^-16
 
 enum { TC_COUNT = 0, TC_UNION = 1, TC_BORDER = 2, TC_VERIFY = 3 };
@@ -92,6 +92,9 @@ struct TcArgs {
     unsigned *status;
     unsigned long long *ctr;  // [6] band pairs, [7] verify: disagreements outside the band, [8] max |w - exact|
     int col_chunk;            // column tiles per work item
+    int2 *edges;              // union pass: core-core neighbour pairs, cap_per_cta per CTA
+    int *edges_used;          // edges written by each CTA
+    int edge_cap_per_cta;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -127,13 +130,29 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
+// try_wait with a suspend-time hint: a thread whose phase is not complete
+// sleeps (issuing nothing) until the phase completes or about 0.5 ms pass.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(500000u)
+        : "memory");
+    return ok != 0;
+}
+
 // Bounded wait: about two seconds, or until another role has given up.
+// Waiting threads sleep inside try_wait, so they take no issue slots from the
+// epilogue warps sharing their SM sub-partition.
 __device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     while (true) {
-        for (int i = 0; i < 32; ++i)
-            if (mbar_try_wait(bar, parity)) return true;
+        for (int i = 0; i < 8; ++i)
+            if (mbar_try_wait_sleep(bar, parity)) return true;
         if (*abort_flag) return false;
         if (globaltimer() - t0 > 2000000000ull) {
             *abort_flag = 1;
@@ -141,6 +160,14 @@ __device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile 
         }
     }
 }
+
+// Optional pipeline diagnostics (compile with -DDB_TC_WAIT_STATS): cycles each
+// role spends blocked on each barrier, summed into ctr[9..14].
+#ifdef DB_TC_WAIT_STATS
+#define TC_WAIT(acc, expr) ({ long long _t0 = clock64(); bool _r = (expr); acc += clock64() - _t0; _r; })
+#else
+#define TC_WAIT(acc, expr) (expr)
+#endif
 
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile(
@@ -181,7 +208,10 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// 32 consecutive accumulator columns of this thread's TMEM lane (no wait).
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t *r) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -191,7 +221,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 // Shared-memory matrix descriptor: no swizzle, K-major, LBO = 128 B (next core
@@ -236,24 +265,46 @@ struct __align__(16) Smem {
     uint64_t t_full[2], t_empty[2];
     uint32_t tmem_base;
     int abort_flag;
+    int edge_used;
 };
 
-// Work item w: row tile rt = w / nchunk, column tiles [c0, c1).
+// Work item w: column chunk ch = w / nrt and row tile rt = w % nrt, so the
+// CTAs running at one time share their column chunk and its B tiles come from
+// L2; column tiles [c0, c1) of the chunk.
 __device__ __forceinline__ bool item_range(const TcArgs &a, int w, int nR, int nC, int &rt, int &c0, int &c1) {
     const int nrt = (nR + TM - 1) / TM, nct = (nC + TN - 1) / TN;
     const int nchunk = (nct + a.col_chunk - 1) / a.col_chunk;
     if (w >= nrt * nchunk) return false;
-    rt = w / nchunk;
-    const int ch = w - rt * nchunk;
+    const int ch = w / nrt;
+    rt = w - ch * nrt;
     c0 = ch * a.col_chunk;
     c1 = min(nct, c0 + a.col_chunk);
     if (a.upper) c0 = max(c0, (rt * TM) / TN);  // pairs i < j only: skip tiles left of the diagonal
     return true;
 }
 
+// Rare path of the epilogue: a pair that may be a neighbour.  Returns bit 0 =
+// neighbour, bit 1 = it was inside the rounding band and was rechecked.
+template <bool BF16>
+__device__ __noinline__ int decide_candidate(float wv, float alpha, float rho_p, float rho_q, const int16_t *v16,
+                                             int K, int p, int q, int T) {
+    const bool sure = BF16 ? (fmaf(-rho_p, rho_q, wv) >= alpha) : (wv > alpha + (float)FP16_BAND);
+    if (sure) return 1;
+    return (exact_sqdist(v16, K, p, q) <= T ? 1 : 0) | 2;
+}
+
+__device__ __noinline__ void unite_pair(int *parent, int p, int q, unsigned *status) {
+    db::uf_unite(parent, p, q, status);
+}
+
+
+template <int PASS, bool BF16>
 __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    Smem &S = *reinterpret_cast<Smem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    // Align by pointer arithmetic on the shared array (not through an integer),
+    // so the compiler keeps shared-space loads, stores and atomics.
+    const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
+    Smem &S = *reinterpret_cast<Smem *>(smem_raw + pad);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nR = *a.nR_ptr, nC = *a.nC_ptr;
     const int nrt = (nR + TM - 1) / TM, nct = (nC + TN - 1) / TN;
@@ -274,6 +325,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(TcArgs a) {
             mbar_init(&S.b_empty[i], 1 + EPI_WARPS);
         }
         S.abort_flag = 0;
+        S.edge_used = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -285,6 +337,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(TcArgs a) {
     tc_fence_after();
     const uint32_t tmem = S.tmem_base;
     const int K = a.K, KG = K / 8;
+    long long w_prod = 0, w_mma_b = 0, w_mma_t = 0, w_epi = 0, t_start = clock64();
+    (void)w_prod, (void)w_mma_b, (void)w_mma_t, (void)w_epi, (void)t_start;
     const uint32_t a_bytes = (uint32_t)(TM * K * 2), b_bytes = (uint32_t)(TN * K * 2);
 
     if (warp == 0) {
@@ -301,7 +355,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(TcArgs a) {
                 bulk_g2s(&S.metaA[ab], a.metaR + rt, sizeof(MetaBlock), &S.a_full[ab]);
                 for (int ct = c0; ct < c1; ++ct, ++t) {
                     const int s = t % NSTAGE;
-                    if (!mbar_wait(&S.b_empty[s], ((t / NSTAGE) & 1) ^ 1, abort_flag)) break;
+                    if (!TC_WAIT(w_prod, mbar_wait(&S.b_empty[s], ((t / NSTAGE) & 1) ^ 1, abort_flag))) break;
                     mbar_arrive_expect_tx(&S.b_full[s], b_bytes + 2 * sizeof(MetaBlock));
                     bulk_g2s(S.B[s], a.opC + (size_t)ct * TN * K, b_bytes, &S.b_full[s]);
                     bulk_g2s(&S.metaB[s][0], a.metaC + 2 * ct, 2 * sizeof(MetaBlock), &S.b_full[s]);
@@ -314,7 +368,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(TcArgs a) {
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            const uint32_t idesc = idesc_f16(a.bf16 != 0);
+            const uint32_t idesc = idesc_f16(BF16);
             int t = 0, ia = 0;
             bool clean = true;
             for (int w = blockIdx.x; w < nitems && !*abort_flag; w += gridDim.x, ++ia) {
@@ -326,8 +380,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(TcArgs a) {
                 bool ok = true;
                 for (int ct = c0; ct < c1; ++ct, ++t) {
                     const int s = t % NSTAGE, b = t & 1;
-                    if (!mbar_wait(&S.b_full[s], (t / NSTAGE) & 1, abort_flag) ||
-                        !mbar_wait(&S.t_empty[b], ((t >> 1) & 1) ^ 1, abort_flag)) {
+                    if (!TC_WAIT(w_mma_b, mbar_wait(&S.b_full[s], (t / NSTAGE) & 1, abort_flag)) ||
+                        !TC_WAIT(w_mma_t, mbar_wait(&S.t_empty[b], ((t >> 1) & 1) ^ 1, abort_flag))) {
                         ok = false;
                         break;
                     }
@@ -375,7 +429,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(TcArgs a) {
             int rt, c0, c1;
             item_range(a, w, nR, nC, rt, c0, c1);
             const int ab = ia & 1;
-            if (!mbar_wait(&S.a_full[ab], (ia >> 1) & 1, abort_flag)) break;
+            if (!__all_sync(0xffffffffu, mbar_wait(&S.a_full[ab], (ia >> 1) & 1, abort_flag))) break;
             const float beta_p = S.metaA[ab].beta[r], rho_p = S.metaA[ab].rho[r];
             const int p = S.metaA[ab].idx[r];
             __syncwarp();
@@ -383,66 +437,147 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(TcArgs a) {
             const int i_row = rt * TM + r;  // list index of this row
             const bool row_ok = i_row < nR && p >= 0;
             const float alpha = beta_p - (float)a.T;  // |v_p|^2 - T, exact
-            const float alo = alpha - (float)FP16_BAND, ahi = alpha + (float)FP16_BAND;
+            const float alo = alpha - (float)FP16_BAND;
             int cnt = 0, bmin = INT_MAX;
             bool ok = true;
             for (int ct = c0; ct < c1; ++ct, ++t) {
                 const int s = t % NSTAGE, b = t & 1;
-                if (!mbar_wait(&S.t_full[b], (t >> 1) & 1, abort_flag)) {
+                // warp-uniform outcome: the accumulator loads below are warp-collective
+                if (!__all_sync(0xffffffffu, TC_WAIT(w_epi, mbar_wait(&S.t_full[b], (t >> 1) & 1, abort_flag)))) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
                 const MetaBlock &mc = S.metaB[s][half];
 #pragma unroll 1
-                for (int ch = 0; ch < 4; ++ch) {
-                    const int cb = ch * 32;  // column within this warp's 128-column half
-                    uint32_t g[32];
-                    tmem_ld32(tmem + lane_base + (uint32_t)(b * TN + half * 128 + cb), g);
-                    if (!row_ok) continue;
-#pragma unroll
-                    for (int j4 = 0; j4 < 8; ++j4) {
-                        const float4 b4 = *reinterpret_cast<const float4 *>(&mc.beta[cb + 4 * j4]);
-                        float4 r4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (a.bf16) r4 = *reinterpret_cast<const float4 *>(&mc.rho[cb + 4 * j4]);
-                        const float bq[4] = {b4.x, b4.y, b4.z, b4.w}, rq[4] = {r4.x, r4.y, r4.z, r4.w};
-#pragma unroll
-                        for (int jj = 0; jj < 4; ++jj) {
-                            const int j = 4 * j4 + jj;
-                            const float gv = __uint_as_float(g[j]);
-                            const float wv = fmaf(2.f, gv, -bq[jj]);  // 2G - |v_q|^2
-                            if (a.pass == TC_VERIFY) {
-                                const int q = mc.idx[cb + j];
-                                if (q < 0) continue;
-                                const int D = exact_sqdist(a.v16, K, p, q);
-                                // 2G exactly, from integers: |v_p|^2 + |v_q|^2 - D (the betas are exact)
-                                const long long two_g = (long long)beta_p + (long long)bq[jj] - D;
-                                const double err = fabs(2.0 * (double)gv - (double)two_g);
-                                maxerr = max(maxerr, (unsigned)fmin(err, 4.0e9));
-                                const bool nb_exact = D <= a.T;
-                                const float del = a.bf16 ? rho_p * rq[jj] : (float)FP16_BAND;
-                                const bool in_band = fabsf(wv - alpha) <= del;
-                                band_cnt += in_band;
-                                if (!in_band && ((wv >= alpha) != nb_exact)) ++bad_cnt;
-                                cnt += nb_exact;
-                                continue;
-                            }
-                            // the common case: certainly not a neighbour
-                            if (a.bf16 ? (fmaf(rho_p, rq[jj], wv) < alpha) : (wv < alo)) continue;
+                for (int hc = 0; hc < 2; ++hc) {
+                    const int cb = hc * 64;  // column within this warp's 128-column half
+                    uint32_t g[64];
+                    const uint32_t taddr = tmem + lane_base + (uint32_t)(b * TN + half * 128 + cb);
+                    tmem_ld32_nowait(taddr, g);
+                    tmem_ld32_nowait(taddr + 32, g + 32);
+                    tmem_wait_ld();
+                    if (PASS == TC_VERIFY) {
+                        if (!row_ok) continue;
+#pragma unroll 1
+                        for (int j = 0; j < 64; ++j) {
                             const int q = mc.idx[cb + j];
                             if (q < 0) continue;
-                            if (a.upper && i_row >= ct * TN + half * 128 + cb + j) continue;  // i < j only
-                            bool nb;
-                            if (a.bf16 ? (fmaf(-rho_p, rq[jj], wv) >= alpha) : (wv > ahi)) {
-                                nb = true;
-                            } else {  // inside the rounding band: decide exactly
-                                ++band_cnt;
-                                nb = exact_sqdist(a.v16, K, p, q) <= a.T;
-                            }
-                            if (!nb) continue;
-                            if (a.pass == TC_COUNT) ++cnt;
-                            else if (a.pass == TC_UNION) db::uf_unite(a.parent, p, q, a.status);
-                            else bmin = min(bmin, q);
+                            const float gv = __uint_as_float(g[j & 63]);
+                            const float wv = fmaf(2.f, gv, -mc.beta[cb + j]);
+                            const int D = exact_sqdist(a.v16, K, p, q);
+                            // 2G exactly, from integers: |v_p|^2 + |v_q|^2 - D (the betas are exact)
+                            const long long two_g = (long long)beta_p + (long long)mc.beta[cb + j] - D;
+                            const double err = fabs(2.0 * (double)gv - (double)two_g);
+                            maxerr = max(maxerr, (unsigned)fmin(err, 4.0e9));
+                            const bool nb_exact = D <= a.T;
+                            const float del = BF16 ? rho_p * mc.rho[cb + j] : (float)FP16_BAND;
+                            const bool in_band = fabsf(wv - alpha) <= del;
+                            band_cnt += in_band;
+                            if (!in_band && ((wv >= alpha) != nb_exact)) ++bad_cnt;
+                            cnt += nb_exact;
+                        }
+                        continue;
+                    }
+                    if (PASS == TC_COUNT && !BF16) {
+                        // FP16 count: G is exact, so sat(2G - |v_q|^2 + 1 - alpha) is
+                        // exactly 1 for a neighbour (T - D + 1 >= 1) and 0 otherwise;
+                        // three branch-free FP32 ops per pair.
+                        const float c1 = 1.f - alpha;
+                        float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+                        for (int j4 = 0; j4 < 16; ++j4) {
+                            const float4 b4 = *reinterpret_cast<const float4 *>(&mc.beta[cb + 4 * j4]);
+                            acc0 += __saturatef(fmaf(2.f, __uint_as_float(g[4 * j4 + 0]), -b4.x) + c1);
+                            acc1 += __saturatef(fmaf(2.f, __uint_as_float(g[4 * j4 + 1]), -b4.y) + c1);
+                            acc0 += __saturatef(fmaf(2.f, __uint_as_float(g[4 * j4 + 2]), -b4.z) + c1);
+                            acc1 += __saturatef(fmaf(2.f, __uint_as_float(g[4 * j4 + 3]), -b4.w) + c1);
+                        }
+                        if (row_ok) cnt += (int)(acc0 + acc1);
+                        continue;
+                    }
+                    // Union / border / BF16: per pair one FFMA (two for BF16); the
+                    // maxima of the eight strided column groups (j mod 8) come from
+                    // the first three levels of an FMNMX tree.  Only groups whose
+                    // maximum can reach the threshold are rescanned.
+                    float wv[64];
+#pragma unroll
+                    for (int j4 = 0; j4 < 16; ++j4) {
+                        const float4 b4 = *reinterpret_cast<const float4 *>(&mc.beta[cb + 4 * j4]);
+                        wv[4 * j4 + 0] = fmaf(2.f, __uint_as_float(g[4 * j4 + 0]), -b4.x);
+                        wv[4 * j4 + 1] = fmaf(2.f, __uint_as_float(g[4 * j4 + 1]), -b4.y);
+                        wv[4 * j4 + 2] = fmaf(2.f, __uint_as_float(g[4 * j4 + 2]), -b4.z);
+                        wv[4 * j4 + 3] = fmaf(2.f, __uint_as_float(g[4 * j4 + 3]), -b4.w);
+                        if (BF16) {
+                            const float4 r4 = *reinterpret_cast<const float4 *>(&mc.rho[cb + 4 * j4]);
+                            wv[4 * j4 + 0] = fmaf(rho_p, r4.x, wv[4 * j4 + 0]);
+                            wv[4 * j4 + 1] = fmaf(rho_p, r4.y, wv[4 * j4 + 1]);
+                            wv[4 * j4 + 2] = fmaf(rho_p, r4.z, wv[4 * j4 + 2]);
+                            wv[4 * j4 + 3] = fmaf(rho_p, r4.w, wv[4 * j4 + 3]);
+                        }
+                    }
+#pragma unroll
+                    for (int w2 = 32; w2 >= 8; w2 >>= 1)
+#pragma unroll
+                        for (int j = 0; j < w2; ++j) wv[j] = fmaxf(wv[j], wv[j + w2]);
+                    const float thr = BF16 ? alpha : alpha - (float)FP16_BAND;
+                    const float mx = fmaxf(fmaxf(fmaxf(wv[0], wv[1]), fmaxf(wv[2], wv[3])),
+                                           fmaxf(fmaxf(wv[4], wv[5]), fmaxf(wv[6], wv[7])));
+                    const bool need = row_ok && mx >= thr;
+                    if (!__any_sync(0xffffffffu, need)) continue;
+                    // Rare path: the lanes that need it build the 64-bit mask of
+                    // possible neighbours (for FP16 exactly the neighbours), then
+                    // walk only its set bits.
+                    uint64_t mask = 0;
+                    if (need) {
+                        const int col_lim = a.upper ? (i_row - (ct * TN + half * 128)) : -1;  // cols <= this: j <= i
+#pragma unroll
+                        for (int j = 0; j < 64; ++j) {
+                            const float w1 = fmaf(2.f, __uint_as_float(g[j]), -mc.beta[cb + j]);
+                            const bool c = BF16 ? (fmaf(rho_p, mc.rho[cb + j], w1) >= alpha) : (w1 >= alpha);
+                            mask |= (uint64_t)(c && (cb + j) > col_lim) << j;
+                        }
+                    }
+                    uint64_t nbm = 0;  // confirmed neighbours among the mask
+                    for (uint64_t mm = mask; mm; mm &= mm - 1) {
+                        const int j = __ffsll((long long)mm) - 1;
+                        const int q = mc.idx[cb + j];
+                        if (q < 0) continue;
+                        bool nb = true;
+                        if (BF16) {
+                            // recompute 2G - |v_q|^2 for column j from the accumulator copy in g
+                            float gj = 0.f;
+#pragma unroll
+                            for (int k = 0; k < 64; ++k)
+                                if (k == j) gj = __uint_as_float(g[k]);
+                            const float wj = fmaf(2.f, gj, -mc.beta[cb + j]);
+                            const int res = decide_candidate<BF16>(wj, alpha, rho_p, mc.rho[cb + j], a.v16, K, p, q, a.T);
+                            band_cnt += res >> 1;
+                            nb = res & 1;
+                        }
+                        if (!nb) continue;
+                        nbm |= 1ull << j;
+                        if (PASS == TC_COUNT) ++cnt;
+                        else if (PASS == TC_BORDER) bmin = min(bmin, q);
+                    }
+                    if (PASS == TC_UNION) {
+                        // one shared-memory atomic per warp reserves every lane's edges
+                        const int ne = __popcll(nbm);
+                        int incl = ne;
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                            if (lane >= o) incl += y;
+                        }
+                        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+                        int base = 0;
+                        if (lane == 31 && tot) base = atomicAdd(&S.edge_used, tot);
+                        base = __shfl_sync(0xffffffffu, base, 31) + incl - ne;
+                        int2 *dst = a.edges + (size_t)blockIdx.x * a.edge_cap_per_cta;
+                        for (uint64_t mm = nbm; mm; mm &= mm - 1, ++base) {
+                            const int q = mc.idx[cb + __ffsll((long long)mm) - 1];
+                            if (base < a.edge_cap_per_cta) dst[base] = make_int2(p, q);
+                            else unite_pair(a.parent, p, q, a.status);  // list full: unite here
                         }
                     }
                 }
@@ -454,8 +589,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(TcArgs a) {
                 }
             }
             if (row_ok) {
-                if ((a.pass == TC_COUNT || a.pass == TC_VERIFY) && cnt) atomicAdd(a.count + p, cnt);
-                if (a.pass == TC_BORDER && bmin != INT_MAX) atomicMin(a.border + p, bmin);
+                if ((PASS == TC_COUNT || PASS == TC_VERIFY) && cnt) atomicAdd(a.count + p, cnt);
+                if (PASS == TC_BORDER && bmin != INT_MAX) atomicMin(a.border + p, bmin);
             }
             if (!ok) break;
         }
@@ -464,6 +599,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(TcArgs a) {
         if (maxerr) atomicMax(a.ctr + 8, (unsigned long long)maxerr);
     }
 
+#ifdef DB_TC_WAIT_STATS
+    if (threadIdx.x == 0) atomicAdd(a.ctr + 9, (unsigned long long)w_prod);
+    if (threadIdx.x == 32) {
+        atomicAdd(a.ctr + 10, (unsigned long long)w_mma_b);
+        atomicAdd(a.ctr + 11, (unsigned long long)w_mma_t);
+        atomicAdd(a.ctr + 13, (unsigned long long)(clock64() - t_start));
+    }
+    if (threadIdx.x == 64) atomicAdd(a.ctr + 12, (unsigned long long)w_epi);
+#endif
     // ---------------- teardown ----------------
     tc_fence_before();
     __syncthreads();
@@ -479,7 +623,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(TcArgs a) {
         __syncthreads();
     }
     tc_fence_after();
+    if (PASS == TC_UNION && threadIdx.x == 0) a.edges_used[blockIdx.x] = min(S.edge_used, a.edge_cap_per_cta);
     if (warp == 1) tmem_dealloc(tmem, 512);
+}
+
+// Unites the core-core neighbour pairs the union pass listed (one thread per pair).
+__global__ void tc_edges_kernel(const int2 *__restrict__ edges, const int *__restrict__ used, int nctas, int cap,
+                                int *parent, unsigned *status) {
+    const int64_t total = (int64_t)nctas * cap;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / cap), k = (int)(e - (int64_t)c * cap);
+        if (k >= used[c]) continue;
+        const int2 pq = edges[e];
+        db::uf_unite(parent, pq.x, pq.y, status);
+    }
 }
 
 // ---------------- preparation kernels ----------------
@@ -580,6 +737,24 @@ __global__ void core_flags_kernel(int n, const uint8_t *__restrict__ core, int *
 
 size_t tc_smem_bytes() { return sizeof(Smem) + 1024; }
 
+template <int PASS, bool BF16>
+cudaError_t launch_pass_t(const TcArgs &a, int sms, cudaStream_t st) {
+    static bool attr = false;  // one process-wide attribute per instantiation
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(tc_pass_kernel<PASS, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)tc_smem_bytes());
+        if (e) return e;
+        attr = true;
+    }
+    tc_pass_kernel<PASS, BF16><<<sms, NTHREADS, tc_smem_bytes(), st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int PASS>
+cudaError_t launch_pass(const TcArgs &a, int sms, cudaStream_t st) {
+    return a.bf16 ? launch_pass_t<PASS, true>(a, sms, st) : launch_pass_t<PASS, false>(a, sms, st);
+}
+
 }  // namespace
 
 // Host launcher of the whole tensor-core all-pairs pipeline.
@@ -588,13 +763,6 @@ cudaError_t launch_allpairs_tc(const DbWork &w, const float *x, int64_t n64, int
     const int n = (int)n64;
     const int K = ((d + 15) / 16) * 16;
     const int n_pad = ((n + TN - 1) / TN) * TN;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(tc_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)tc_smem_bytes());
-        if (e) return e;
-        attr_set = true;
-    }
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -621,14 +789,13 @@ cudaError_t launch_allpairs_tc(const DbWork &w, const float *x, int64_t n64, int
     a.status = w.status;
     a.ctr = w.ctr;
     a.col_chunk = 32;
-    const size_t smem = tc_smem_bytes();
     // pass 1: all x all -> neighbour counts
     a.opR = a.opC = w.opAll;
     a.metaR = a.metaC = reinterpret_cast<const MetaBlock *>(w.metaAll);
     a.nR_ptr = a.nC_ptr = lens + 2;
     a.pass = TC_COUNT;
     a.upper = 0;
-    tc_pass_kernel<<<sms, NTHREADS, smem, st>>>(a);
+    if ((e = launch_pass<TC_COUNT>(a, sms, st))) return e;
     w.marks->kernel("tc_count", st);
     // core flags, parent, border init (shared with the SIMT path)
     launch_core_init(w, n, min_pts, st);
@@ -653,8 +820,13 @@ cudaError_t launch_allpairs_tc(const DbWork &w, const float *x, int64_t n64, int
     a.nR_ptr = a.nC_ptr = lens + 0;
     a.pass = TC_UNION;
     a.upper = 1;
-    tc_pass_kernel<<<sms, NTHREADS, smem, st>>>(a);
+    a.edges = w.edges;
+    a.edges_used = w.edges_used;
+    a.edge_cap_per_cta = (int)std::min<int64_t>(w.edge_cap / sms, INT_MAX);
+    if ((e = launch_pass<TC_UNION>(a, sms, st))) return e;
     w.marks->kernel("tc_union", st);
+    tc_edges_kernel<<<152 * 8, 256, 0, st>>>(w.edges, w.edges_used, sms, a.edge_cap_per_cta, w.parent, w.status);
+    w.marks->kernel("tc_union_edges", st);
     // pass 3: non-core x core -> smallest core neighbour
     a.opR = w.opNon;
     a.metaR = reinterpret_cast<const MetaBlock *>(w.metaNon);
@@ -664,7 +836,7 @@ cudaError_t launch_allpairs_tc(const DbWork &w, const float *x, int64_t n64, int
     a.nC_ptr = lens + 0;
     a.pass = TC_BORDER;
     a.upper = 0;
-    tc_pass_kernel<<<sms, NTHREADS, smem, st>>>(a);
+    if ((e = launch_pass<TC_BORDER>(a, sms, st))) return e;
     w.marks->kernel("tc_border", st);
     return cudaGetLastError();
 }
@@ -677,9 +849,7 @@ cudaError_t launch_tc_verify(const DbWork &w, const float *x, int64_t n64, int32
     const int n = (int)n64;
     const int K = ((d + 15) / 16) * 16;
     const int n_pad = ((n + TN - 1) / TN) * TN;
-    cudaError_t e = cudaFuncSetAttribute(tc_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)tc_smem_bytes());
-    if (e) return e;
+    cudaError_t e;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -703,6 +873,5 @@ cudaError_t launch_tc_verify(const DbWork &w, const float *x, int64_t n64, int32
     a.metaR = a.metaC = reinterpret_cast<const MetaBlock *>(w.metaAll);
     a.nR_ptr = a.nC_ptr = lens + 2;
     a.pass = TC_VERIFY;
-    tc_pass_kernel<<<sms, NTHREADS, tc_smem_bytes(), st>>>(a);
-    return cudaGetLastError();
+    return launch_pass<TC_VERIFY>(a, sms, st);
 }

@@ -8,7 +8,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/dbscan.h"
+#include "dbscan.h"  // include/ is on the include path
 
 // Device-side error bits, OR-ed into the plan's status word.
 #define DB_EBIT_NOT_QUANTISED 1u
@@ -153,6 +153,9 @@ struct DbWork {
     void *metaAll, *metaCore, *metaNon;  // per-point metadata blocks (16 B per row)
     int32_t *list_a, *list_b;  // core / non-core index lists [cap_n]
     int32_t *tc_lens;       // [0] cores, [1] non-cores, [2] all
+    int2 *edges;            // core-core neighbour pairs found by the union pass
+    int32_t *edges_used;    // per CTA
+    int64_t edge_cap;       // total edge slots
     PhaseMarks *marks;      // host-side timing marks of the owning plan
 };
 
