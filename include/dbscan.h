@@ -201,10 +201,19 @@ typedef struct dbscan_instance {
 } dbscan_instance;
 
 /* Clusters `count` independent instances (each as dbscan_run would, with the
- * plan's label mode; all-pairs SIMT arithmetic).  Uses its own device
- * workspace, grown on demand and kept by the plan.  Synchronous; per_inst
- * (host, nullable, `count` entries) receives per-instance counts. */
+ * plan's label mode; all-pairs SIMT arithmetic, 1 <= d <= 16, larger d gives
+ * DBSCAN_ERR_UNSUPPORTED).  All instances run in one graph-captured launch
+ * sequence of persistent kernels that share a work queue of (instance, row
+ * tile, column chunk) items.  The first call autotunes the chunk size and grid
+ * on the given batch.  Uses its own device workspace, grown on demand and kept
+ * by the plan.  Synchronous; per_inst (host, nullable, `count` entries)
+ * receives per-instance counts. */
 int dbscan_batch(dbscan_plan *plan, const dbscan_instance *inst, int32_t count, dbscan_stats *per_inst);
+
+/* The configuration dbscan_batch's autotuner picked for this plan on its first
+ * call: column tiles (64 points each) per work item and resident blocks per SM.
+ * DBSCAN_ERR_NOT_FOUND before the first batch. */
+int dbscan_batch_config(dbscan_plan *plan, int32_t *chunk_tiles, int32_t *blocks_per_sm);
 
 /* ---- Served form: continuous batching of submitted jobs under an HBM budget ---- */
 

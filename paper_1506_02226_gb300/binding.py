@@ -80,6 +80,7 @@ _SIGS = {
     "dbscan_plan_counters": (ctypes.c_int, [c_p, c_p, c_i32]),
     "dbscan_plan_phase_times": (ctypes.c_int, [c_p, c_i32, c_p, c_p, c_p]),
     "dbscan_batch": (ctypes.c_int, [c_p, c_p, c_i32, c_p]),
+    "dbscan_batch_config": (ctypes.c_int, [c_p, c_p, c_p]),
     "dbscan_serve_opts_default": (None, [c_p]),
     "dbscan_serve_create": (ctypes.c_int, [c_p, c_p]),
     "dbscan_serve_submit": (ctypes.c_int, [c_p, c_p, c_p]),
@@ -217,6 +218,12 @@ def dbscan_run_noalloc(points: int, n: int, d: int, eps: float, min_pts: int, la
                        stream: int | None = None) -> int:
     """Status code of the call; clusters without any device allocation (see include/dbscan.h)."""
     return lib().dbscan_run_noalloc(points, n, d, eps, min_pts, label_mode, labels_out, stream)
+
+
+def dbscan_batch_config(plan: int) -> tuple[int, int]:
+    ch, bps = c_i32(), c_i32()
+    _check(lib().dbscan_batch_config(plan, ctypes.byref(ch), ctypes.byref(bps)), "dbscan_batch_config")
+    return ch.value, bps.value
 
 
 def dbscan_serve_opts_default() -> dbscan_serve_opts:

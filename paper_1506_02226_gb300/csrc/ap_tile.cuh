@@ -1,0 +1,215 @@
+// ap_tile.cuh — the all-pairs SIMT tile (Section IV-A/IV-B), shared by the
+// single-instance kernels (pairs_simt.cu) and the batched kernels (batch.cu).
+//
+// The score of a pair is T + 1 - D(p,q), an integer, and q is a neighbour
+// iff score >= 1; __saturatef(score) is then exactly 0 or 1.
+//   MODE_GRAM   (d <= 8): score = (T+1 - |p|^2) - |q|^2 + sum_k (2u_pk) u_qk in
+//               FP32.  Every partial sum is an integer of magnitude below
+//               2*d*1023^2 <= 16,744,464 < 2^24, so FP32 holds it exactly.
+//   MODE_DIRECT (FP32, d <= 16, or T + 1 <= 2^24): score = (T+1) - sum (u_pk-u_qk)^2.
+//               Partial sums only decrease; they are exact while >= -2^24, and
+//               once below that they stay below 1, so the decision is exact.
+//   MODE_INT    otherwise: the same in int32.
+#pragma once
+
+#include <climits>
+
+#include "internal.cuh"
+
+namespace aptile {
+
+constexpr int BM = 64, BN = 64, NT = 256;
+enum { PASS_COUNT = 0, PASS_UNION = 1, PASS_BORDER = 2 };
+enum { MODE_GRAM = 0, MODE_DIRECT = 1, MODE_INT = 2 };
+
+struct ApArgs {
+    const float *P;  // packed units, row stride DP
+    int n;
+    float Tp1;       // T + 1 (exact: T + 1 <= 2^24 whenever a float mode is used)
+    int Tc;          // T clamped to d*1023^2
+    const uint8_t *core;
+    int *count;
+    int *parent;
+    int *border;
+    unsigned *status;
+    int ntiles;
+    int splits;
+};
+
+
+// One block's work: row tile rt against column tiles [ct_begin, ct_end).
+// Called by the all-pairs kernel below and, once per work item, by the
+// batched kernel (batch.cu).  All branches that return are block-uniform.
+template <int DP, int MODE, int PASS>
+__device__ __forceinline__ void ap_tile_body(const ApArgs &a, int rt, int ct_begin, int ct_end) {
+    __shared__ __align__(16) float As[DP][BM];
+    __shared__ __align__(16) float Bs[DP][BN];
+    __shared__ float An[BM], Bn[BN];
+    __shared__ uint8_t Ac[BM], Bc[BN];
+
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int row0 = rt * BM;
+    __syncthreads();  // the previous work item of this block is done with the tiles
+
+    // ---- the row tile stays in shared memory for the whole block (Section IV-A) ----
+    for (int e = tid; e < BM * DP; e += NT) {
+        int r = e / DP, k = e - (e / DP) * DP;
+        int row = row0 + r;
+        As[k][r] = (row < a.n) ? a.P[(size_t)row * DP + k] : 0.f;
+    }
+    if (PASS != PASS_COUNT)
+        for (int r = tid; r < BM; r += NT) Ac[r] = (row0 + r < a.n) ? a.core[row0 + r] : 0;
+    __syncthreads();
+    if (MODE == MODE_GRAM) {
+        // Per-row terms hoisted out of the pair loop (Section IV-B): T+1-|p|^2 and 2p.
+        for (int r = tid; r < BM; r += NT) {
+            float nrm = 0.f;
+#pragma unroll
+            for (int k = 0; k < DP; ++k) {
+                float v = As[k][r];
+                nrm = fmaf(v, v, nrm);
+                As[k][r] = 2.f * v;
+            }
+            An[r] = a.Tp1 - nrm;
+        }
+    }
+    int want_rows = 1;
+    if (PASS == PASS_UNION || PASS == PASS_BORDER) {
+        int mine = 0;
+        for (int r = tid; r < BM; r += NT)
+            if (row0 + r < a.n) mine |= (PASS == PASS_UNION) ? (Ac[r] != 0) : (Ac[r] == 0);
+        want_rows = __syncthreads_or(mine);
+    } else {
+        __syncthreads();
+    }
+    if (!want_rows) return;
+
+    float rc[4] = {0.f, 0.f, 0.f, 0.f};
+    int bm[4] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX};
+
+    for (int ct = ct_begin; ct < ct_end; ++ct) {
+        const int col0 = ct * BN;
+        __syncthreads();
+        if (MODE == MODE_GRAM) {
+            if (tid < BN) {
+                const int col = col0 + tid;
+                float nrm = 0.f;
+                if (col < a.n) {
+#pragma unroll
+                    for (int k = 0; k < DP; ++k) {
+                        float v = a.P[(size_t)col * DP + k];
+                        Bs[k][tid] = v;
+                        nrm = fmaf(v, v, nrm);
+                    }
+                    Bn[tid] = -nrm;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < DP; ++k) Bs[k][tid] = 0.f;
+                    Bn[tid] = -1e30f;  // padding column: never a neighbour
+                }
+            }
+        } else {
+            for (int e = tid; e < BN * DP; e += NT) {
+                int c = e / DP, k = e - (e / DP) * DP;
+                int col = col0 + c;
+                Bs[k][c] = (col < a.n) ? a.P[(size_t)col * DP + k] : (MODE == MODE_INT ? 0.f : 1e18f);
+            }
+        }
+        int want_cols = 1;
+        if (PASS != PASS_COUNT) {
+            int mine = 0;
+            for (int c = tid; c < BN; c += NT) {
+                int col = col0 + c;
+                uint8_t f = (col < a.n) ? a.core[col] : 0;
+                Bc[c] = f;
+                mine |= f;
+            }
+            want_cols = __syncthreads_or(mine);
+        } else {
+            __syncthreads();
+        }
+        if (!want_cols) continue;
+
+        float acc[4][4];
+        int iacc[4][4];
+        if (MODE == MODE_GRAM) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = An[ty * 4 + i] + Bn[tx * 4 + j];
+        } else if (MODE == MODE_DIRECT) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = a.Tp1;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) iacc[i][j] = a.Tc;
+        }
+#pragma unroll
+        for (int k = 0; k < DP; ++k) {
+            const float4 av = *reinterpret_cast<const float4 *>(&As[k][ty * 4]);
+            const float4 bv = *reinterpret_cast<const float4 *>(&Bs[k][tx * 4]);
+            const float ar[4] = {av.x, av.y, av.z, av.w};
+            const float br[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (MODE == MODE_GRAM) {
+                        acc[i][j] = fmaf(ar[i], br[j], acc[i][j]);
+                    } else if (MODE == MODE_DIRECT) {
+                        float df = ar[i] - br[j];
+                        acc[i][j] = fmaf(-df, df, acc[i][j]);
+                    } else {
+                        int di = (int)ar[i] - (int)br[j];
+                        iacc[i][j] -= di * di;
+                    }
+                }
+        }
+        // ---- fused consumer (Section IV-B: no distance is stored) ----
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = ty * 4 + i, p = row0 + r;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = tx * 4 + j, q = col0 + c;
+                bool nb;
+                if (MODE == MODE_INT) nb = (iacc[i][j] >= 0) && (q < a.n);
+                else nb = acc[i][j] >= 1.f;
+                if (PASS == PASS_COUNT) {
+                    if (MODE == MODE_INT) rc[i] += nb ? 1.f : 0.f;
+                    else rc[i] += __saturatef(acc[i][j]);
+                } else if (PASS == PASS_UNION) {
+                    if (nb && p < q && Ac[r] && Bc[c]) db::uf_unite(a.parent, p, q, a.status);
+                } else {
+                    if (nb && p < a.n && !Ac[r] && Bc[c]) bm[i] = min(bm[i], q);
+                }
+            }
+        }
+    }
+
+    if (PASS == PASS_COUNT) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            int v = (int)rc[i];
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            const int p = row0 + ty * 4 + i;
+            if (tx == 0 && p < a.n && v) atomicAdd(a.count + p, v);
+        }
+    } else if (PASS == PASS_BORDER) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            int v = bm[i];
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+            const int p = row0 + ty * 4 + i;
+            if (tx == 0 && p < a.n && v != INT_MAX) atomicMin(a.border + p, v);
+        }
+    }
+}
+
+}  // namespace aptile

@@ -823,6 +823,9 @@ cudaError_t launch_allpairs_tc(const DbWork &w, const float *x, int64_t n64, int
     a.edges = w.edges;
     a.edges_used = w.edges_used;
     a.edge_cap_per_cta = (int)std::min<int64_t>(w.edge_cap / sms, INT_MAX);
+    // CTAs without work items leave their slot untouched: clear every slot so no
+    // edges of an earlier run are replayed.
+    if ((e = cudaMemsetAsync(w.edges_used, 0, sizeof(int) * (size_t)sms, st))) return e;
     if ((e = launch_pass<TC_UNION>(a, sms, st))) return e;
     w.marks->kernel("tc_union", st);
     tc_edges_kernel<<<152 * 8, 256, 0, st>>>(w.edges, w.edges_used, sms, a.edge_cap_per_cta, w.parent, w.status);

@@ -295,3 +295,18 @@ def test_full_size_high_d_workload():
     np.testing.assert_array_equal(lab, want_lab)
     lab2, _ = gpu_labels(inst.points, inst.eps, inst.min_pts)
     np.testing.assert_array_equal(lab2, want_lab)
+
+
+def test_tensor_core_plan_reused_across_sizes():
+    """One plan, instances of shrinking size: nothing of an earlier run may leak
+    into a later one (per-CTA edge lists, counters, packed operands)."""
+    from paper_1506_02226_gb300.api import Plan
+    with Plan(max_n=12_000, max_d=32, precision=B.DBSCAN_PREC_FP16_GRAM, grid=B.DBSCAN_GRID_OFF) as p:
+        for seed, n, d in ((1, 11_000, 16), (2, 7519, 16), (3, 3000, 32), (4, 500, 16), (5, 9000, 32)):
+            spread = int(6 + 3 * np.sqrt(d))
+            x = _blobs(seed, n, d, spread=spread)
+            eps = float(np.float32(1.3 * spread * np.sqrt(d) / 1024))
+            lab, cnt, core, st = p.run_detail(torch.from_numpy(x).cuda(), eps, 6)
+            want_lab, want_cnt, _ = oracle.dbscan(x, eps, 6)
+            np.testing.assert_array_equal(cnt.cpu().numpy(), want_cnt)
+            np.testing.assert_array_equal(lab.cpu().numpy(), want_lab)
