@@ -221,23 +221,42 @@ typedef struct dbscan_server dbscan_server;
 
 typedef struct dbscan_serve_opts {
     int32_t device;
-    int32_t slots;            /* jobs that may be on the device at once */
-    int64_t hbm_budget_bytes; /* admission cap on the summed workspace of in-flight jobs */
+    int32_t slots;            /* jobs that may be on the device at once (each slot: one stream, one plan) */
+    int64_t hbm_budget_bytes; /* admission cap on the summed workspace of the jobs on the device */
     int32_t label_mode;       /* DBSCAN_LABEL_* */
     int32_t precision;        /* DBSCAN_PREC_* */
-    int32_t reserved[8];
+    int64_t max_n;            /* largest job accepted (slot plans are sized for it) */
+    int32_t max_d;            /* largest d accepted */
+    int32_t max_queue;        /* jobs waiting for a slot before submit answers DBSCAN_ERR_BUSY */
+    int32_t reserved[4];
 } dbscan_serve_opts;
 
+/* Defaults: device 0, 8 slots, 120 GiB budget, root-index labels, PREC_AUTO,
+ * max_n 500,000, max_d 64, max_queue 1,000,000. */
 void dbscan_serve_opts_default(dbscan_serve_opts *opts);
+
+/* Starts a server: allocates every slot's plan and starts the worker thread
+ * that admits queued jobs to free slots (continuous batching: a job is
+ * admitted as soon as a slot and enough of the HBM budget are free, while
+ * other jobs still run), enqueues them on the slot's stream and completes them
+ * when their events fire. */
 int dbscan_serve_create(dbscan_server **out, const dbscan_serve_opts *opts);
-/* Queues a job; the instance's device buffers must stay valid until it is
- * done.  *job_id receives its id.  Thread-safe. */
+/* Queues a job (Section I's three steps on one instance, as dbscan_run).  The
+ * instance's device buffers must stay valid until it is done.  *job_id
+ * receives its id.  DBSCAN_ERR_ARG for a bad instance or n > max_n / d >
+ * max_d; DBSCAN_ERR_BUSY when max_queue jobs already wait.  Thread-safe. */
 int dbscan_serve_submit(dbscan_server *srv, const dbscan_instance *inst, uint64_t *job_id);
-/* *done = 1 once the job's labels are written; its status is returned then. */
+/* *done = 1 once the job's labels are written; the job's own status is
+ * returned then (0 otherwise).  DBSCAN_ERR_NOT_FOUND for an unknown or
+ * released id.  Thread-safe. */
 int dbscan_serve_poll(dbscan_server *srv, uint64_t job_id, int32_t *done);
-/* Waits up to timeout_us (< 0: forever) for the job.  DBSCAN_ERR_TIMEOUT if it
- * is not done by then.  latency_us (nullable) receives submit-to-done time. */
+/* Waits up to timeout_us (< 0: forever) for the job and releases it.
+ * DBSCAN_ERR_TIMEOUT if it is not done by then (the job stays).  latency_us
+ * (nullable) receives its submit-to-done time in microseconds.  Returns the
+ * job's status.  Thread-safe. */
 int dbscan_serve_wait(dbscan_server *srv, uint64_t job_id, int64_t timeout_us, double *latency_us);
+/* Waits for every admitted job, stops the worker and frees the slots.  Jobs
+ * still queued are dropped. */
 int dbscan_serve_destroy(dbscan_server *srv);
 
 /* ---- Entry point that allocates nothing (the paper has no counterpart) ----

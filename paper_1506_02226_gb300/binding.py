@@ -64,7 +64,8 @@ class dbscan_tc_report(ctypes.Structure):
 
 class dbscan_serve_opts(ctypes.Structure):
     _fields_ = [("device", c_i32), ("slots", c_i32), ("hbm_budget_bytes", c_i64), ("label_mode", c_i32),
-                ("precision", c_i32), ("reserved", c_i32 * 8)]
+                ("precision", c_i32), ("max_n", c_i64), ("max_d", c_i32), ("max_queue", c_i32),
+                ("reserved", c_i32 * 4)]
 
 
 _SIGS = {

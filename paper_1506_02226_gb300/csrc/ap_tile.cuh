@@ -34,6 +34,7 @@ struct ApArgs {
     unsigned *status;
     int ntiles;
     int splits;
+    int early;  // count pass: stop a row tile once every row has this many (0: exact counts)
 };
 
 
@@ -85,7 +86,20 @@ __device__ __forceinline__ void ap_tile_body(const ApArgs &a, int rt, int ct_beg
     if (!want_rows) return;
 
     float rc[4] = {0.f, 0.f, 0.f, 0.f};
+    int prior[4] = {0, 0, 0, 0};  // count pass with early exit: counts other work already added
+    if (PASS == PASS_COUNT && a.early > 0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int p = row0 + ty * 4 + i;
+            prior[i] = p < a.n ? a.count[p] : INT_MAX / 2;
+        }
+        int done = 1;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) done &= prior[i] >= a.early;
+        if (__syncthreads_and(done)) return;  // every row is already core
+    }
     int bm[4] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX};
+    int rootp[4] = {-2, -2, -2, -2};  // union: last known root of each row's set
 
     for (int ct = ct_begin; ct < ct_end; ++ct) {
         const int col0 = ct * BN;
@@ -183,11 +197,44 @@ __device__ __forceinline__ void ap_tile_body(const ApArgs &a, int rt, int ct_beg
                     if (MODE == MODE_INT) rc[i] += nb ? 1.f : 0.f;
                     else rc[i] += __saturatef(acc[i][j]);
                 } else if (PASS == PASS_UNION) {
-                    if (nb && p < q && Ac[r] && Bc[c]) db::uf_unite(a.parent, p, q, a.status);
+                    if (nb && p < q && Ac[r] && Bc[c]) {
+                        // q already hangs under p's last known root: same set, skip
+                        // (a plain, possibly stale read is enough: a stale parent
+                        // equal to the root still means the same set)
+                        if (a.parent[q] != rootp[i])
+                            rootp[i] = db::uf_unite_root(a.parent, p, q, a.status);
+                    }
                 } else {
                     if (nb && p < a.n && !Ac[r] && Bc[c]) bm[i] = min(bm[i], q);
                 }
             }
+        }
+        if (PASS == PASS_COUNT && a.early > 0 && ((ct - ct_begin) & 3) == 3) {
+            // every 4 tiles: stop once every row of the tile has min_pts neighbours
+            int done = 1;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                int v = (int)rc[i];
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                done &= prior[i] + v >= a.early;
+            }
+            if (__syncthreads_and(done)) break;  // counts are flushed after the loop
+        }
+        if (PASS == PASS_BORDER) {
+            // Columns grow with ct, so a row's first hit is its smallest core
+            // neighbour in this block's range: stop once every row has one (or
+            // needs none).
+            int done = 1;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                int v = bm[i];
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+                const int r = ty * 4 + i;
+                done &= (v != INT_MAX) || (row0 + r >= a.n) || Ac[r];
+            }
+            if (__syncthreads_and(done)) break;
         }
     }
 

@@ -124,9 +124,15 @@ __global__ void __launch_bounds__(NT) batch_pass_kernel(const BInst *__restrict_
         a.status = status;
         a.ntiles = I.ntiles;
         a.splits = 1;
-        if (I.dp == 16) ap_tile_body<16, MODE_DIRECT, PASS>(a, rt, ct0, ct1);
-        else if (I.dp == 8) ap_tile_body<8, MODE_GRAM, PASS>(a, rt, ct0, ct1);
-        else ap_tile_body<4, MODE_GRAM, PASS>(a, rt, ct0, ct1);
+        a.early = I.min_pts;  // batch outputs labels only: counts may stop at min_pts
+        switch (I.dp) {  // block-uniform: one instance per work item
+            case 1: ap_tile_body<1, MODE_GRAM, PASS>(a, rt, ct0, ct1); break;
+            case 2: ap_tile_body<2, MODE_GRAM, PASS>(a, rt, ct0, ct1); break;
+            case 3: ap_tile_body<3, MODE_GRAM, PASS>(a, rt, ct0, ct1); break;
+            case 4: ap_tile_body<4, MODE_GRAM, PASS>(a, rt, ct0, ct1); break;
+            case 8: ap_tile_body<8, MODE_GRAM, PASS>(a, rt, ct0, ct1); break;
+            default: ap_tile_body<16, MODE_DIRECT, PASS>(a, rt, ct0, ct1); break;
+        }
     }
 }
 
@@ -308,7 +314,7 @@ int64_t build_table(const dbscan_instance *inst, int count, int ch, BInst *t, in
         I.labels = in.labels_out;
         I.n = (int)in.n;
         I.d = in.d;
-        I.dp = in.d <= 4 ? 4 : (in.d <= 8 ? 8 : 16);
+        I.dp = dp_for(in.d);  // 1, 2, 3, 4, 8 or 16
         I.mode = I.dp == 16 ? MODE_DIRECT : MODE_GRAM;
         I.Tc = (int)Tc;
         I.Tp1 = (float)(Tc + 1);
@@ -328,7 +334,10 @@ int64_t build_table(const dbscan_instance *inst, int count, int ch, BInst *t, in
     return items;
 }
 
-cudaError_t enqueue_batch(BatchState *b, int label_mode, bool stats, int ch, int bps, cudaStream_t st) {
+cudaError_t enqueue_batch(BatchState *b, int label_mode, bool stats, int ch, int bps, cudaStream_t st,
+                          PhaseMarks *pm = nullptr) {
+    PhaseMarks off;
+    if (!pm) pm = &off;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -341,21 +350,28 @@ cudaError_t enqueue_batch(BatchState *b, int label_mode, bool stats, int ch, int
     if ((e = cudaMemsetAsync(b->d_count, 0, 4 * (size_t)b->cap_points, st))) return e;
     if (stats && (e = cudaMemsetAsync(b->d_istats, 0, 16 * (size_t)b->cap_count, st))) return e;
     batch_prep_kernel<<<egrid, 256, 0, st>>>(b->d_table, b->d_hdr, b->d_pinst, b->d_P, b->d_status);
+    pm->kernel("batch_prep", st);
     batch_pass_kernel<PASS_COUNT><<<pgrid, NT, 0, st>>>(b->d_table, b->d_hdr, ch, b->d_work + 0, b->d_P, b->d_count,
                                                         b->d_core, b->d_parent, b->d_border, b->d_status);
+    pm->kernel("batch_count", st);
     batch_core_init_kernel<<<egrid, 256, 0, st>>>(b->d_table, b->d_hdr, b->d_pinst, b->d_count, b->d_core,
                                                   b->d_parent, b->d_border);
+    pm->kernel("batch_core_init", st);
     batch_pass_kernel<PASS_UNION><<<pgrid, NT, 0, st>>>(b->d_table, b->d_hdr, ch, b->d_work + 1, b->d_P, b->d_count,
                                                         b->d_core, b->d_parent, b->d_border, b->d_status);
+    pm->kernel("batch_union", st);
     batch_pass_kernel<PASS_BORDER><<<pgrid, NT, 0, st>>>(b->d_table, b->d_hdr, ch, b->d_work + 2, b->d_P,
                                                          b->d_count, b->d_core, b->d_parent, b->d_border, b->d_status);
+    pm->kernel("batch_border", st);
     batch_label_kernel<<<egrid, 256, 0, st>>>(b->d_table, b->d_hdr, b->d_pinst, b->d_core, b->d_parent, b->d_border,
                                               b->d_flags, stats ? b->d_istats : nullptr);
+    pm->kernel("batch_label", st);
     if ((e = cudaGetLastError())) return e;
     if (label_mode == DBSCAN_LABEL_COMPACT) {
-        if ((e = launch_exclusive_scan(b->d_flags, b->d_scan, b->cap_points, b->d_part, b->part_cap, st, &b->marks)))
+        if ((e = launch_exclusive_scan(b->d_flags, b->d_scan, b->cap_points, b->d_part, b->part_cap, st, pm)))
             return e;
         batch_compact_kernel<<<egrid, 256, 0, st>>>(b->d_table, b->d_hdr, b->d_pinst, b->d_scan);
+        pm->kernel("batch_compact", st);
     }
     if (stats && (e = cudaMemcpyAsync(b->h_istats, b->d_istats, 16 * (size_t)b->cap_count, cudaMemcpyDeviceToHost,
                                       st)))
@@ -474,8 +490,13 @@ extern "C" int dbscan_batch(dbscan_plan *plan, const dbscan_instance *inst, int3
         b->tuned = true;
     }
     prepare(b->ch);
-    s = batch_graph_launch(b, label_mode, stats, st);
-    if (s) return s;
+    if (plan->opts.profile) {  // per-kernel events: run the sequence uncaptured
+        plan->marks.begin(st);
+        if (enqueue_batch(b, label_mode, stats, b->ch, b->bps, st, &plan->marks)) return DBSCAN_ERR_CUDA;
+    } else {
+        s = batch_graph_launch(b, label_mode, stats, st);
+        if (s) return s;
+    }
     if (cudaStreamSynchronize(st) != cudaSuccess) return DBSCAN_ERR_CUDA;
     if (cur >= 0 && cur != plan->opts.device) cudaSetDevice(cur);
     const unsigned bits = *b->h_status;

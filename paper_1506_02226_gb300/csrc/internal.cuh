@@ -68,6 +68,25 @@ __device__ __forceinline__ void uf_unite(int *parent, int a, int b, unsigned *st
     atomicOr(status, DB_EBIT_TIMEOUT);
 }
 
+// Union that also returns a root of the merged set (a hint for callers that
+// cache it: the value is the set's root at some moment, so any point whose
+// parent equals it is in the set).
+__device__ __forceinline__ int uf_unite_root(int *parent, int a, int b, unsigned *status) {
+    for (int it = 0; it < (1 << 24); ++it) {
+        a = uf_find(parent, a);
+        b = uf_find(parent, b);
+        if (a == b) return a;
+        if (a > b) {
+            int t = a;
+            a = b;
+            b = t;
+        }
+        if (atomicCAS(parent + b, b, a) == b) return a;
+    }
+    atomicOr(status, DB_EBIT_TIMEOUT);
+    return -1;
+}
+
 // 2^-10 grid check of one coordinate: finite, 0 <= x < 1, 1024 x integral.
 __device__ __forceinline__ bool on_grid(float x, int &u) {
     float s = x * 1024.0f;  // exact: scaling by a power of two

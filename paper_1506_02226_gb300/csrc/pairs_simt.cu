@@ -125,7 +125,7 @@ cudaError_t launch_core_init(const DbWork &w, int64_t n, int32_t min_pts, cudaSt
 }
 
 cudaError_t launch_allpairs_simt(const DbWork &w, int64_t n64, int32_t d, int32_t dp, int64_t Tc, int32_t min_pts,
-                                 bool /*exact_counts*/, cudaStream_t st) {
+                                 bool exact_counts, cudaStream_t st) {
     const int n = (int)n64;
     ApArgs a;
     a.P = w.P;
@@ -138,6 +138,7 @@ cudaError_t launch_allpairs_simt(const DbWork &w, int64_t n64, int32_t d, int32_
     a.border = w.border;
     a.status = w.status;
     a.ntiles = (n + BM - 1) / BM;
+    a.early = exact_counts ? 0 : min_pts;
     // Enough blocks to fill 152 SMs a few times over, splitting the column range.
     int splits = (4 * 152 + a.ntiles - 1) / a.ntiles;
     a.splits = std::max(1, std::min(splits, a.ntiles));
