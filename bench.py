@@ -395,6 +395,86 @@ def run_batch(args):
     print(json.dumps(out))
 
 
+def run_serve(args):
+    """Jobs through the server: closed-loop saturation, then Poisson arrivals at
+    0.7x and 0.9x of it, with per-job submit-to-done latency."""
+    from paper_1506_02226_gb300 import build as cuda_build
+    cuda_build.build()
+    import threading
+    import torch
+    from paper_1506_02226_gb300 import binding as B
+
+    pool = [inputs.serve_job(i) for i in range(args.serve_pool)]
+    dev = []
+    for inst in pool:
+        x = torch.from_numpy(inst.points).cuda()
+        lab = torch.empty(inst.n, dtype=torch.int32, device="cuda")
+        s = B.dbscan_instance()
+        s.points, s.n, s.d, s.eps, s.min_pts, s.labels_out = x.data_ptr(), inst.n, inst.d, inst.eps, inst.min_pts, \
+            lab.data_ptr()
+        dev.append((x, lab, s))
+    o = B.dbscan_serve_opts_default()
+    o.slots = args.serve_slots
+    o.max_n = max(i.n for i in pool)
+    o.max_d = 64
+    srv = B.dbscan_serve_create(o)
+    njobs = args.serve_jobs
+
+    def run(arrivals):
+        ids, lats = [None] * njobs, [0.0] * njobs
+        t0 = time.perf_counter()
+
+        def submitter():
+            for k in range(njobs):
+                if arrivals is not None:
+                    dt = arrivals[k] - (time.perf_counter() - t0)
+                    if dt > 0:
+                        time.sleep(dt)
+                ids[k] = B.dbscan_serve_submit(srv, dev[k % len(dev)][2])
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        for k in range(njobs):
+            while ids[k] is None:
+                time.sleep(50e-6)
+            st, lat = B.dbscan_serve_wait(srv, ids[k], -1)
+            if st != 0:
+                raise RuntimeError(f"serve job {k} failed: {st}")
+            lats[k] = lat
+        th.join()
+        wall = time.perf_counter() - t0
+        return njobs / wall, lats
+
+    for k in range(min(len(dev), 2 * args.serve_slots)):  # warm-up: first launches, graph/attribute setup
+        B.dbscan_serve_wait(srv, B.dbscan_serve_submit(srv, dev[k][2]), -1)
+    clocks = ClockSampler(torch.cuda.current_device())
+    sat, lat_closed = run(None)
+    levels = {}
+    for frac in (0.7, 0.9):
+        arr = inputs.serve_arrivals(njobs, frac * sat)
+        jobs_s, lats = run(arr)
+        levels[str(frac)] = {"offered_jobs_per_s": frac * sat, "jobs_per_s": jobs_s,
+                             "p50_ms": float(np.percentile(lats, 50)) / 1e3,
+                             "p99_ms": float(np.percentile(lats, 99)) / 1e3}
+    clk = clocks.stop()
+    B.dbscan_serve_destroy(srv)
+    mix = {d: sum(1 for i in pool if i.d == d) for d in (2, 3, 32)}
+    out = {
+        "metric": "served jobs/s", "value": sat, "unit": "jobs/s", "n_gpus": 1, "steps": njobs, "warmup":
+            min(len(dev), 2 * args.serve_slots), "ms_per_step": 1e3 / sat, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"serve: {njobs} jobs drawn cyclically from {len(pool)} seeded jobs, n log-uniform "
+                               f"1k..500k, d in {{2,3,32}} ({mix}), blob+noise, per-job eps/min_pts",
+                   "slots": args.serve_slots, "hbm_budget_gib": 120,
+                   "admission": "slot-bound: every job's footprint is far below the budget"},
+        "closed_loop": {"jobs_per_s": sat, "p50_ms": float(np.percentile(lat_closed, 50)) / 1e3,
+                        "p99_ms": float(np.percentile(lat_closed, 99)) / 1e3},
+        "poisson": levels,
+        "e2e": None, "roofline": None, "cpu_baseline": None, "gpu_launches": None, "clocks": clk,
+    }
+    print(json.dumps(out))
+
+
 def run_ours(args, wl_name):
     from paper_1506_02226_gb300 import build as cuda_build
     cuda_build.build()  # in-tree, only recompiles what changed
@@ -545,10 +625,13 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch"], default="lowd2")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch", "serve"], default="lowd2")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU baseline (for profiler runs)")
     ap.add_argument("--n", type=int, default=0, help="cluster a uniform subsample of this many points instead")
     ap.add_argument("--batch-count", type=int, default=4096, help="instances of the batch workload")
+    ap.add_argument("--serve-jobs", type=int, default=10_000, help="jobs of the serve workload")
+    ap.add_argument("--serve-pool", type=int, default=192, help="distinct seeded jobs the serve workload cycles")
+    ap.add_argument("--serve-slots", type=int, default=8, help="server slots")
     ap.add_argument("--cpu-sample", type=int, default=128, help="instances the oracle runs for the batch baseline")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture, for the roofline")
@@ -562,6 +645,9 @@ def main():
         return
     if args.workload == "batch":
         run_batch(args)
+        return
+    if args.workload == "serve":
+        run_serve(args)
         return
     run_ours(args, args.workload)
 
