@@ -205,6 +205,22 @@ def pair_ops(d: int) -> int:
     return d + 2 if d <= 8 else 2 * d + 1
 
 
+# ------------------------------------------------------------------ replicas
+def max_over_ranks(local_ms: float, dist, device) -> float:
+    """Largest per-rank time (the job finishes when its slowest replica does)."""
+    import torch
+    if dist is None:
+        return local_ms
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms_per_step: float) -> float:
+    """Units all replicas processed per second (weak scaling: each rank runs one replica)."""
+    return world * units_per_rank / (ms_per_step * 1e-3)
+
+
 # ------------------------------------------------------------------ arms
 def run_reference(args, wl_name):
     """The oracle (plain CPU brute force) timed on bounded samples of the workload."""
@@ -541,14 +557,11 @@ def run_ours(args, wl_name):
         clk = clocks.stop()
     if plan.sync() != 0:
         raise RuntimeError("timed run reported an error")
-    total_ms = sum(step_ms)
+    total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
     if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
     ms_per_step = total_ms / args.steps
-    value = world * units / (ms_per_step * 1e-3) / 1e9
+    value = whole_job_rate(units, world, ms_per_step) / 1e9
 
     # end to end: host (pinned) buffers through the C ABI, copies inside the timed region
     host_pts = torch.from_numpy(inst.points).pin_memory()
