@@ -31,9 +31,10 @@
 //            (Section IV-C's merge), adjacent cells in one launch and the
 //            outer ring in a second; a cell pair already in one set is skipped
 //   border   each non-core point finds its smallest-index core neighbour
-//   label    labels from the union-find roots
+//   root     the union-find root of every cell with cores
+//   label    labels (a thread per point)
 // The pair kernels give one warp to one cell at a time and walk candidate
-// cells' points 32 at a time, so neighbour loads are coalesced.
+// cells' points 32 lanes wide, four independent loads per lane in flight.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -257,8 +258,9 @@ struct PairArgs {
 // Count pass (Section IV-B, fused pair test + count).  Per cell A:
 //   |A| >= min_pts and no exact counts: every point is core, no pair test;
 //   |A| >= 32 with exact counts: one lane per point, candidates broadcast;
-//   otherwise: per point, the warp walks the flattened candidates and stops
-//   once the count reaches min_pts (unless exact counts are asked for).
+//   otherwise: per point, the warp walks the flattened candidates, 128 per
+//   step with four independent loads per lane, and stops once the count
+//   reaches min_pts (unless exact counts are asked for).
 // Then the smallest core index of A goes to cell_rep[A], and every core point
 // of A is hung under it in the union-find forest (cells are cliques); other
 // points are their own parent.
@@ -276,11 +278,17 @@ __global__ void __launch_bounds__(256) grid_count_kernel(PairArgs a, int min_pts
         const int *row = a.nbr + (size_t)A * noff;
         int minorig = DB_NONE;
         if (cA >= lim) {
-            for (int i = lane; i < cA; i += 32) {
-                const int p = sA + i, o = a.sidx[p];
-                score[p] = 1;
-                if (core_out) core_out[o] = 1;
-                minorig = min(minorig, o);
+            for (int i0 = lane; i0 < cA; i0 += 128) {
+                int o[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) o[u] = (i0 + 32 * u < cA) ? a.sidx[sA + i0 + 32 * u] : DB_NONE;
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (i0 + 32 * u < cA) {
+                        score[sA + i0 + 32 * u] = 1;
+                        if (core_out) core_out[o[u]] = 1;
+                        minorig = min(minorig, o[u]);
+                    }
             }
         } else if (cA >= 32) {
             for (int i0 = 0; i0 < cA; i0 += 32) {
@@ -325,11 +333,19 @@ __global__ void __launch_bounds__(256) grid_count_kernel(PairArgs a, int min_pts
                         incl = warp_incl_scan(c);
                         total = __shfl_sync(FULL, incl, 31);
                     }
-                    for (int base = 0; base < total && cnt < lim; base += 32) {
-                        const int j = base + lane;
-                        const int q = locate(j, incl, c, s);
-                        const bool hit = j < total && is_nbr<D>(cp, px2, py2, pz2, a.spts[q]);
-                        cnt += __popc(__ballot_sync(FULL, hit));
+                    for (int base = 0; base < total && cnt < lim; base += 128) {
+                        float4 qq[4];
+                        bool val[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int j = base + 32 * u + lane;
+                            const int q = locate(j, incl, c, s);
+                            val[u] = j < total;
+                            qq[u] = val[u] ? a.spts[q] : make_float4(0.f, 0.f, 0.f, -1e30f);
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            cnt += __popc(__ballot_sync(FULL, val[u] && is_nbr<D>(cp, px2, py2, pz2, qq[u])));
                     }
                 }
                 const bool core = cnt >= min_pts;
@@ -345,9 +361,18 @@ __global__ void __launch_bounds__(256) grid_count_kernel(PairArgs a, int min_pts
         minorig = warp_min(minorig);
         if (lane == 0) cell_rep[A] = minorig;
         __syncwarp();
-        for (int i = lane; i < cA; i += 32) {
-            const int p = sA + i, o = a.sidx[p];
-            parent[o] = score[p] ? minorig : o;
+        for (int i0 = lane; i0 < cA; i0 += 128) {
+            int o[4];
+            uint8_t sc[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool v = i0 + 32 * u < cA;
+                o[u] = v ? a.sidx[sA + i0 + 32 * u] : 0;
+                sc[u] = v ? score[sA + i0 + 32 * u] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (i0 + 32 * u < cA) parent[o[u]] = sc[u] ? minorig : o[u];
         }
     }
 }
@@ -356,14 +381,19 @@ __global__ void __launch_bounds__(256) grid_count_kernel(PairArgs a, int min_pts
 // (cells are cliques).  Lanes look at up to 32 neighbouring cells B of A at
 // once (offsets [o_begin, o_end), each cell pair from its smaller key); for
 // every B with cores that is not yet in A's set, the warp searches for one
-// core pair within eps — lanes over the larger cell, a loop over the smaller —
-// and unites the two sets at the first hit.
+// core pair within eps and unites the two sets at the first hit.  The search
+// stages up to 128 points of the smaller cell in the warp's shared memory
+// (coalesced loads) and runs the lanes over the larger cell against them.
 template <int D>
 __global__ void __launch_bounds__(256) grid_union_kernel(PairArgs a, const uint8_t *__restrict__ score, int *parent,
                                                          unsigned *status, int o_begin, int o_end) {
-    const int lane = threadIdx.x & 31;
+    __shared__ float4 ybuf[8][128];
+    __shared__ uint8_t ycore[8][128];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
     const int ncells = (int)(*a.ctr0 >> 32);
+    float4 *yb = ybuf[wib];
+    uint8_t *yc = ycore[wib];
     for (int A = warp; A < ncells; A += nwarps) {
         const int repA = a.cell_rep[A];
         if (repA == DB_NONE) continue;
@@ -377,31 +407,45 @@ __global__ void __launch_bounds__(256) grid_union_kernel(PairArgs a, const uint8
             bool need = repB != DB_NONE;
             if (need) need = db::uf_find(parent, repA) != db::uf_find(parent, repB);
             unsigned todo = __ballot_sync(FULL, need);
+            bool first = true;
             while (todo) {
                 const int l = __ffs(todo) - 1;
                 todo &= todo - 1;
                 const int Bl = __shfl_sync(FULL, B, l), rB = __shfl_sync(FULL, repB, l);
-                if (l != __ffs(__ballot_sync(FULL, need)) - 1) {  // an earlier union may have joined them
+                if (!first) {  // an earlier union may have joined them
                     int same = 0;
                     if (lane == 0) same = db::uf_find(parent, repA) == db::uf_find(parent, rB);
                     if (__shfl_sync(FULL, same, 0)) continue;
                 }
+                first = false;
                 const int sB = a.cell_start[Bl], cB = a.cell_count[Bl];
                 const bool swap = cB > cA;  // lanes over the larger cell
                 const int sX = swap ? sB : sA, cX = swap ? cB : cA, sY = swap ? sA : sB, cY = swap ? cA : cB;
                 bool found = false;
-                for (int x0 = 0; x0 < cX && !found; x0 += 32) {
-                    const int xi = x0 + lane;
-                    const bool vx = xi < cX && score[sX + xi];
-                    if (!__any_sync(FULL, vx)) continue;
-                    const float4 px = a.spts[sX + (xi < cX ? xi : 0)];
-                    const float cp = a.g.Tp1 + px.w, px2 = 2.f * px.x, py2 = 2.f * px.y, pz2 = 2.f * px.z;
-                    for (int y = sY; y < sY + cY; ++y) {
-                        if (!score[y]) continue;
-                        const bool hit = vx && is_nbr<D>(cp, px2, py2, pz2, a.spts[y]);
-                        if (__any_sync(FULL, hit)) {
-                            found = true;
-                            break;
+                for (int y0 = 0; y0 < cY && !found; y0 += 128) {
+                    const int ny = min(128, cY - y0);
+                    __syncwarp();
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int k = lane + 32 * u;
+                        if (k < ny) {
+                            yb[k] = a.spts[sY + y0 + k];
+                            yc[k] = score[sY + y0 + k];
+                        }
+                    }
+                    __syncwarp();
+                    for (int x0 = 0; x0 < cX && !found; x0 += 32) {
+                        const int xi = x0 + lane;
+                        const bool vx = xi < cX && score[sX + xi];
+                        if (!__any_sync(FULL, vx)) continue;
+                        const float4 px = a.spts[sX + (xi < cX ? xi : 0)];
+                        const float cp = a.g.Tp1 + px.w, px2 = 2.f * px.x, py2 = 2.f * px.y, pz2 = 2.f * px.z;
+                        for (int k = 0; k < ny; ++k) {
+                            if (!yc[k]) continue;
+                            if (__any_sync(FULL, vx && is_nbr<D>(cp, px2, py2, pz2, yb[k]))) {
+                                found = true;
+                                break;
+                            }
                         }
                     }
                 }
@@ -417,6 +461,7 @@ __global__ void __launch_bounds__(256) grid_union_kernel(PairArgs a, const uint8
 // with fewer than min_pts points hold non-core points.  The own cell's
 // representative is a neighbour (cliques); other cells are skipped when their
 // representative (their smallest core index) cannot beat the current best.
+// Candidates are walked 128 per step, four independent loads per lane.
 template <int D>
 __global__ void __launch_bounds__(256) grid_border_kernel(PairArgs a, int min_pts, const uint8_t *__restrict__ score,
                                                           int *__restrict__ bord) {
@@ -427,8 +472,7 @@ __global__ void __launch_bounds__(256) grid_border_kernel(PairArgs a, int min_pt
     for (int A = warp; A < ncells; A += nwarps) {
         const int sA = a.cell_start[A], cA = a.cell_count[A];
         if (cA >= min_pts) continue;
-        // any non-core point here?
-        bool nc = false;
+        bool nc = false;  // any non-core point here?
         for (int i = lane; i < cA; i += 32) nc |= !score[sA + i];
         if (!__any_sync(FULL, nc)) continue;
         const int repA = a.cell_rep[A];
@@ -453,13 +497,22 @@ __global__ void __launch_bounds__(256) grid_border_kernel(PairArgs a, int min_pt
                 if (r >= b) c = 0;  // cannot beat b
                 const int incl = warp_incl_scan(c), total = __shfl_sync(FULL, incl, 31);
                 int best = b;
-                for (int base = 0; base < total; base += 32) {
-                    const int j = base + lane;
-                    const int q = locate(j, incl, c, s);
-                    if (j < total && score[q]) {
-                        const int qi = a.sidx[q];
-                        if (qi < best && is_nbr<D>(cp, px2, py2, pz2, a.spts[q])) best = qi;
+                for (int base = 0; base < total; base += 128) {
+                    float4 qq[4];
+                    int qi[4];
+                    uint8_t sc[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int j = base + 32 * u + lane;
+                        const int q = locate(j, incl, c, s);
+                        const bool v = j < total;
+                        sc[u] = v ? score[q] : 0;
+                        qi[u] = v ? a.sidx[q] : DB_NONE;
+                        qq[u] = v ? a.spts[q] : make_float4(0.f, 0.f, 0.f, -1e30f);
                     }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (sc[u] && qi[u] < best && is_nbr<D>(cp, px2, py2, pz2, qq[u])) best = qi[u];
                 }
                 b = warp_min(best);
             }
@@ -468,52 +521,68 @@ __global__ void __launch_bounds__(256) grid_border_kernel(PairArgs a, int min_pt
     }
 }
 
-// Labels, one warp per cell: core points take their set's root (the cluster's
-// smallest core index, found once per cell), border points the root of their
-// chosen core neighbour, noise -1.  Also counts core / border / noise points
-// and clusters (a cluster's root is the representative of its own cell).
-__global__ void __launch_bounds__(256) grid_label_kernel(PairArgs a, const uint8_t *__restrict__ score,
-                                                         const int *__restrict__ bord, int *parent,
-                                                         int *__restrict__ labels, unsigned long long *ctr) {
-    __shared__ int red[4][8];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
-    const int ncells = (int)(*a.ctr0 >> 32);
-    int nc = 0, nb = 0, nn = 0, nr = 0;
-    for (int A = warp; A < ncells; A += nwarps) {
-        const int sA = a.cell_start[A], cA = a.cell_count[A];
-        const int repA = a.cell_rep[A];
+// Root of every cell with cores, once per cell (a thread per cell), and the
+// number of clusters: a cluster's root is the representative of its own cell.
+__global__ void grid_cell_root_kernel(const unsigned long long *ctr0, const int *__restrict__ cell_rep, int *parent,
+                                      int *__restrict__ cell_root, unsigned long long *ctr) {
+    __shared__ int red[8];
+    const int ncells = (int)(*ctr0 >> 32);
+    int nr = 0;
+    for (int A = blockIdx.x * blockDim.x + threadIdx.x; A < ncells; A += gridDim.x * blockDim.x) {
+        const int rep = cell_rep[A];
         int root = -1;
-        if (lane == 0 && repA != DB_NONE) root = db::uf_find(parent, repA);
-        root = __shfl_sync(FULL, root, 0);
-        if (lane == 0 && repA != DB_NONE && root == repA) ++nr;
-        for (int i = lane; i < cA; i += 32) {
-            const int p = sA + i, o = a.sidx[p];
-            int lab;
-            if (score[p]) {
-                lab = root;
-                ++nc;
-            } else {
-                const int b = bord[p];
-                if (b == DB_NONE) {
-                    lab = -1;
-                    ++nn;
-                } else {
-                    lab = db::uf_find(parent, b);
-                    ++nb;
-                }
-            }
-            labels[o] = lab;
+        if (rep != DB_NONE) {
+            root = db::uf_find(parent, rep);
+            nr += root == rep;
         }
+        cell_root[A] = root;
     }
-    int v[4] = {nc, nb, nn, nr};
+    for (int o = 16; o > 0; o >>= 1) nr += __shfl_xor_sync(FULL, nr, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nr;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        if (t) atomicAdd(ctr + 5, (unsigned long long)t);
+    }
+}
+
+// Labels, a thread per grouped point: core points take their cell's root (the
+// cluster's smallest core index), border points the root of their chosen core
+// neighbour, noise -1.  Also counts core / border / noise points.
+__global__ void grid_label_kernel(int n, const int *__restrict__ sidx, const int *__restrict__ scell,
+                                  const uint8_t *__restrict__ score, const int *__restrict__ cell_root,
+                                  const int *__restrict__ bord, int *parent, int *__restrict__ labels,
+                                  unsigned long long *ctr) {
+    __shared__ int red[3][8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int nc = 0, nb = 0, nn = 0;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const int orig = sidx[p];
+        int lab;
+        if (score[p]) {
+            lab = cell_root[scell[p]];
+            ++nc;
+        } else {
+            const int b = bord[p];
+            if (b == DB_NONE) {
+                lab = -1;
+                ++nn;
+            } else {
+                lab = db::uf_find(parent, b);
+                ++nb;
+            }
+        }
+        labels[orig] = lab;
+    }
+    int v[3] = {nc, nb, nn};
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 3; ++k) {
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(FULL, v[k], o);
         if (lane == 0) red[k][wid] = v[k];
     }
     __syncthreads();
-    if (threadIdx.x < 4) {
+    if (threadIdx.x < 3) {
         int t = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[threadIdx.x][w];
         if (t) atomicAdd(ctr + 2 + threadIdx.x, (unsigned long long)t);
@@ -555,7 +624,6 @@ int64_t isqrt64(int64_t v) {
 template <int D>
 cudaError_t grid_pair_passes(const DbWork &w, const GridGeom &g, int n, int min_pts, bool exact, int32_t *labels,
                              int32_t *counts_out, uint8_t *core_out, cudaStream_t st) {
-    (void)n;
     PairArgs a{g, w.ctr, w.spts, w.sidx, w.cell_start, w.cell_count, w.cell_rep, w.cell_key, w.nbr};
     const int wgrid = 152 * 16;  // 8 warps per block, warps stride over the cells
     grid_count_kernel<D><<<wgrid, 256, 0, st>>>(a, min_pts, exact ? 1 : 0, w.score, w.cell_rep, w.parent,
@@ -569,7 +637,11 @@ cudaError_t grid_pair_passes(const DbWork &w, const GridGeom &g, int n, int min_
     }
     grid_border_kernel<D><<<wgrid, 256, 0, st>>>(a, min_pts, w.score, w.border);
     w.marks->kernel("grid_border", st);
-    grid_label_kernel<<<wgrid, 256, 0, st>>>(a, w.score, w.border, w.parent, labels, w.ctr);
+    // the hash cursors are free after the scatter: they hold the cell roots
+    grid_cell_root_kernel<<<152 * 4, 256, 0, st>>>(w.ctr, w.cell_rep, w.parent, w.hcursor, w.ctr);
+    w.marks->kernel("grid_cell_root", st);
+    grid_label_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, w.sidx, w.scell, w.score, w.hcursor, w.border, w.parent,
+                                                       labels, w.ctr);
     w.marks->kernel("grid_label", st);
     return cudaGetLastError();
 }
