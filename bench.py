@@ -553,7 +553,10 @@ def run_ours(args, wl_name):
         if host_units != units:
             raise RuntimeError(f"candidate-pair count mismatch: device {units} host {host_units}")
 
-    plan = Plan(max_n=n, max_d=d, synchronous=False, stream=stream, profile=True, precision=prec)
+    # Timed steps run without per-kernel marks, so the grid path's independent
+    # kernels may overlap on its second stream; per-kernel times come from a
+    # separate profiled plan that runs them one after another.
+    plan = Plan(max_n=n, max_d=d, synchronous=False, stream=stream, profile=False, precision=prec)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     kern: dict[str, list[float]] = {}
@@ -576,12 +579,22 @@ def run_ours(args, wl_name):
             ev1.record(stream)
             ev1.synchronize()
             step_ms.append(ev0.elapsed_time(ev1))
-            for nm, ms in plan.phase_times():
-                kern.setdefault(nm, []).append(ms)
         torch.cuda.synchronize()
         clk = clocks.stop()
     if plan.sync() != 0:
         raise RuntimeError("timed run reported an error")
+    pplan = Plan(max_n=n, max_d=d, synchronous=False, stream=stream, profile=True, precision=prec)
+    with torch.cuda.stream(stream):
+        for r in range(3 + max(5, min(args.steps, 30))):
+            flush.fill_(1)
+            pplan.run(x, inst.eps, inst.min_pts, labels=labels)
+            stream.synchronize()
+            if r >= 3:
+                for nm, ms in pplan.phase_times():
+                    kern.setdefault(nm, []).append(ms)
+    if pplan.sync() != 0:
+        raise RuntimeError("profiled run reported an error")
+    pplan.close()
     total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
     if dist:
         dist.barrier()
@@ -646,6 +659,7 @@ def run_ours(args, wl_name):
         "points_per_s": world * n / (ms_per_step * 1e-3),
         "clusters": st0["n_clusters"], "core": st0["n_core"], "noise": st0["n_noise"],
         "kernels_ms": {k: round(v, 5) for k, v in sorted(avg.items(), key=lambda kv: -kv[1])},
+        "kernels_ms_note": "each kernel alone (a profiled run, kernels serialised, L2 flushed before each run)",
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": units / (e2e_ms * 1e-3) / 1e9, "unit": "G pair-tests/s", "ms_per_step": e2e_ms,

@@ -59,7 +59,9 @@ size_t layout(DbWork &w, const dbscan_opts &o, char *base) {
         w.hbits = bits;
         w.hkey = c.take<uint32_t>(w.hcap);
         w.hcount = c.take<int32_t>(w.hcap);
-        w.hval = c.take<int32_t>(w.hcap);
+        w.hpack = c.take<int2>(w.hcap);
+        w.occ_cap = std::max<int64_t>(int64_t(1) << 15, 4 * n);
+        w.occ = c.take<uint32_t>(w.occ_cap);
         w.hcursor = c.take<int32_t>(w.hcap);
         w.slot_of = c.take<int32_t>(n);
         w.pts4 = c.take<float4>(n);
@@ -70,13 +72,16 @@ size_t layout(DbWork &w, const dbscan_opts &o, char *base) {
         w.cell_start = c.take<int32_t>(n);
         w.cell_count = c.take<int32_t>(n);
         w.cell_rep = c.take<int32_t>(n);
+        w.cell_mid = c.take<float4>(n);
         w.cell_key = c.take<uint32_t>(n);
         const int dg = std::min(o.max_d, 3);
         w.noff_cap = dg == 1 ? 4 : (dg == 2 ? 24 : 124);
         w.nbr = c.take<int32_t>((size_t)n * w.noff_cap);
+        w.ncnt = c.take<int32_t>(n);
     } else {
         w.hcap = 0;
         w.noff_cap = 0;
+        w.occ_cap = 0;
     }
     if (o.max_d >= 16) {
         const int64_t np = (n + 255) / 256 * 256;
@@ -275,6 +280,15 @@ int dbscan_plan_create(dbscan_plan **out, const dbscan_opts *opts) {
             return DBSCAN_ERR_CUDA;
         }
     }
+    if (p->w.hcap > 0) {  // grid path: side stream and fork/join events
+        bool ok = cudaStreamCreateWithFlags(&p->w.side, cudaStreamNonBlocking) == cudaSuccess;
+        for (int i = 0; i < 4 && ok; ++i)
+            ok = cudaEventCreateWithFlags(&p->w.fj[i], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            dbscan_plan_destroy(p);
+            return DBSCAN_ERR_CUDA;
+        }
+    }
     if (cudaMallocHost(&p->h_status, sizeof(unsigned) * 4) != cudaSuccess ||
         cudaMallocHost(&p->h_ctr, sizeof(unsigned long long) * 16) != cudaSuccess ||
         cudaEventCreate(&p->ev0) != cudaSuccess || cudaEventCreate(&p->ev1) != cudaSuccess) {
@@ -303,6 +317,10 @@ int dbscan_plan_destroy(dbscan_plan *p) {
     if (p->marks.start) cudaEventDestroy(p->marks.start);
     for (int i = 0; i < PhaseMarks::kMax; ++i)
         if (p->marks.ev[i]) cudaEventDestroy(p->marks.ev[i]);
+    if (p->w.side) cudaStreamSynchronize(p->w.side);
+    for (int i = 0; i < 4; ++i)
+        if (p->w.fj[i]) cudaEventDestroy(p->w.fj[i]);
+    if (p->w.side) cudaStreamDestroy(p->w.side);
     delete p;
     return DBSCAN_OK;
 }

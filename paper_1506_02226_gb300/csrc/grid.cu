@@ -20,8 +20,8 @@
 //   prep     grid check, cell key, hash insert, per-cell count
 //   cells    occupied slot -> cell id and point range (block-aggregated)
 //   scatter  points grouped by cell
-//   nbrs     neighbour-cell table (cell x offset -> cell id or -1), adjacent
-//            offsets first
+//   nbrs     neighbour lists: the occupied cells at the kept offsets,
+//            compacted, adjacent offsets first
 //   count    neighbour counts -> core flags (Section IV-B).  A cell with at
 //            least min_pts points makes all its points core with no test; other
 //            points stop counting once they reach min_pts unless exact counts
@@ -33,6 +33,8 @@
 //   border   each non-core point finds its smallest-index core neighbour
 //   root     the union-find root of every cell with cores
 //   label    labels (a thread per point)
+// nbrs runs beside scatter, and border beside union, on the plan's second
+// stream: each pair is independent and latency-bound.
 // The pair kernels give one warp to one cell at a time and walk candidate
 // cells' points 32 lanes wide, four independent loads per lane in flight.
 #include <algorithm>
@@ -43,13 +45,20 @@
 
 namespace {
 
+constexpr unsigned FULL = 0xffffffffu;
+
 __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p) {
     unsigned v;
     asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
 
-__device__ __forceinline__ unsigned hash_slot(unsigned key, int bits) { return (key * 2654435761u) >> (32 - bits); }
+// Cell hash slot: four consecutive keys (four cells in a row along x) share
+// one 32-byte bucket of the packed table, so the lookups of a cell's
+// x-neighbours, made by neighbouring lanes, touch few sectors.
+__device__ __forceinline__ unsigned hash_slot(unsigned key, int bits) {
+    return ((((key >> 2) * 2654435761u) >> (34 - bits)) << 2) | (key & 3u);
+}
 
 __device__ __forceinline__ unsigned cell_key_of(const int *u, const GridGeom &g) {
     unsigned cx = (unsigned)(u[0] / g.c);
@@ -103,9 +112,10 @@ __global__ void grid_prep_kernel(const float *__restrict__ x, int n, GridGeom g,
 constexpr int CELLS_PER_THREAD = 4;
 
 __global__ void grid_cells_kernel(int H, const unsigned *__restrict__ hkey, const int *__restrict__ hcount,
-                                  int *__restrict__ hval, int *__restrict__ hcursor, int *__restrict__ cell_start,
+                                  int2 *__restrict__ hpack, int *__restrict__ hcursor, int *__restrict__ cell_start,
                                   int *__restrict__ cell_count, unsigned *__restrict__ cell_key,
-                                  int *__restrict__ cell_rep, unsigned long long *ctr0) {
+                                  int *__restrict__ cell_rep, unsigned *__restrict__ occ,
+                                  unsigned long long *ctr0) {
     __shared__ int wocc[32], wcnt[32];
     __shared__ unsigned long long base;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -138,21 +148,25 @@ __global__ void grid_cells_kernel(int H, const unsigned *__restrict__ hkey, cons
     int start = (int)(base & 0xffffffffull) + offc + xc - tcnt;
 #pragma unroll
     for (int k = 0; k < CELLS_PER_THREAD; ++k) {
+        const int s = s0 + k;
         if (cnt[k] > 0) {
-            const int s = s0 + k;
+            const unsigned key = hkey[s];
             cell_start[cid] = start;
             cell_count[cid] = cnt[k];
-            cell_key[cid] = hkey[s];
+            cell_key[cid] = key;
             cell_rep[cid] = DB_NONE;
-            hval[s] = cid;
+            hpack[s] = make_int2((int)key, cid);
             hcursor[s] = start;
+            if (occ) atomicOr(occ + (key >> 5), 1u << (key & 31u));
             ++cid;
             start += cnt[k];
+        } else if (s < H) {
+            hpack[s] = make_int2((int)DB_HASH_EMPTY, -1);
         }
     }
 }
 
-__global__ void grid_scatter_kernel(int n, const int *__restrict__ slot_of, int *hcursor, const int *__restrict__ hval,
+__global__ void grid_scatter_kernel(int n, const int *__restrict__ slot_of, int *hcursor, const int2 *__restrict__ hpack,
                                     const float4 *__restrict__ pts4, float4 *__restrict__ spts, int *__restrict__ sidx,
                                     int *__restrict__ scell) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -168,33 +182,86 @@ __global__ void grid_scatter_kernel(int n, const int *__restrict__ slot_of, int 
     const int pos = base + __popc(peers & db::lanemask_lt());
     spts[pos] = pts4[i];
     sidx[pos] = i;
-    scell[pos] = hval[slot];
+    scell[pos] = hpack[slot].y;
 }
 
+// Neighbour lists, a warp per cell: lane l looks up offsets l, l+32, l+64 and
+// l+96 (all loads independent), and the cells found are written compacted,
+// adjacent offsets first; ncnt[A] = (adjacent count << 16) | total count.
+// When the occupancy bitmap of all G^d cells fits its buffer (occ != null),
+// an empty neighbour costs one bit test and no hash probe.
 __global__ void grid_nbr_kernel(GridGeom g, const unsigned long long *ctr0, const unsigned *__restrict__ cell_key,
-                                const unsigned *__restrict__ hkey, const int *__restrict__ hval, int *__restrict__ nbr) {
+                                const int2 *__restrict__ hpack, const unsigned *__restrict__ occ,
+                                int *__restrict__ nbr, int *__restrict__ ncnt) {
+    // Offsets go through shared memory into registers once: lanes indexing the
+    // parameter array with different offsets would serialise on every read.
+    __shared__ char4 soff[128];
+    for (int o = threadIdx.x; o < 128; o += blockDim.x) soff[o] = o < g.noff ? g.off[o] : make_char4(0, 0, 0, 0);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    char4 offr[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) offr[u] = soff[32 * u + lane];
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
     const int ncells = (int)(*ctr0 >> 32);
-    const int64_t total = (int64_t)ncells * g.noff;
     const unsigned mask = (1u << g.hbits) - 1u;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int A = (int)(t / g.noff), o = (int)(t - (int64_t)A * g.noff);
+    const int G = g.G;
+    for (int A = warp; A < ncells; A += nwarps) {
         const unsigned key = cell_key[A];
-        const int G = g.G;
         const int c[3] = {(int)(key % G), (int)((key / G) % G), (int)(key / ((unsigned)G * G))};
-        const char4 off = g.off[o];
-        const int nc[3] = {c[0] + off.x, c[1] + off.y, c[2] + off.z};
-        int res = -1;
-        if (nc[0] >= 0 && nc[0] < G && nc[1] >= 0 && nc[1] < G && nc[2] >= 0 && nc[2] < G) {
-            const unsigned k2 = ((unsigned)nc[2] * G + (unsigned)nc[1]) * G + (unsigned)nc[0];
-            unsigned h = hash_slot(k2, g.hbits);
-            for (unsigned probe = 0; probe <= mask; ++probe) {
-                unsigned cur = hkey[h];
-                if (cur == k2) { res = hval[h]; break; }
-                if (cur == DB_HASH_EMPTY) break;
-                h = (h + 1) & mask;
+        unsigned k2[4];
+        bool in[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int o = 32 * u + lane;
+            in[u] = false;
+            k2[u] = 0;
+            if (o < g.noff) {
+                const char4 off = offr[u];
+                const int nc[3] = {c[0] + off.x, c[1] + off.y, c[2] + off.z};
+                in[u] = nc[0] >= 0 && nc[0] < G && nc[1] >= 0 && nc[1] < G && nc[2] >= 0 && nc[2] < G;
+                k2[u] = ((unsigned)nc[2] * G + (unsigned)nc[1]) * G + (unsigned)nc[0];
             }
         }
-        nbr[t] = res;
+        if (occ) {
+            unsigned wbits[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) wbits[u] = in[u] ? occ[k2[u] >> 5] : 0u;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) in[u] = (wbits[u] >> (k2[u] & 31u)) & 1u;
+        }
+        int2 e[4];
+        unsigned h[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            h[u] = hash_slot(k2[u], g.hbits);
+            e[u] = in[u] ? hpack[h[u]] : make_int2((int)DB_HASH_EMPTY, -1);
+        }
+        int res[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            res[u] = -1;
+            // continue probing past other keys (rare at load factor <= 1/2)
+            for (unsigned probe = 0; probe <= mask; ++probe) {
+                if ((unsigned)e[u].x == k2[u]) { res[u] = e[u].y; break; }
+                if ((unsigned)e[u].x == DB_HASH_EMPTY) break;
+                h[u] = (h[u] + 1) & mask;
+                e[u] = hpack[h[u]];
+            }
+        }
+        int *row = nbr + (size_t)A * g.noff;
+        int nn = 0, nnear = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (32 * u >= g.noff) break;
+            const unsigned hits = __ballot_sync(FULL, res[u] >= 0);
+            if (res[u] >= 0) row[nn + __popc(hits & db::lanemask_lt())] = res[u];
+            const int nl = g.nnear - 32 * u;  // lanes of this chunk with adjacent offsets
+            const unsigned near_lanes = nl <= 0 ? 0u : (nl >= 32 ? FULL : ((1u << nl) - 1u));
+            nnear += __popc(hits & near_lanes);
+            nn += __popc(hits);
+        }
+        if (lane == 0) ncnt[A] = (nnear << 16) | nn;
     }
 }
 
@@ -210,11 +277,10 @@ __device__ __forceinline__ bool is_nbr(float cp, float px2, float py2, float pz2
 }
 
 // ---- warp-cooperative candidate scans -------------------------------------
-// A warp owns one cell A at a time.  The neighbour-cell table row of A is read
-// 32 entries at a time: lane l holds (start, size) of one neighbour cell and an
+// A warp owns one cell A at a time.  The neighbour list of A is read 32
+// entries at a time: lane l holds (start, size) of one neighbour cell and an
 // inclusive prefix of the sizes, so the candidates of those cells form one
 // flattened range that the 32 lanes walk together, 32 candidates per step.
-constexpr unsigned FULL = 0xffffffffu;
 
 __device__ __forceinline__ int warp_incl_scan(int v) {
     const int lane = threadIdx.x & 31;
@@ -251,23 +317,27 @@ struct PairArgs {
     const float4 *spts;
     const int *sidx;
     const int *cell_start, *cell_count, *cell_rep;
+    const float4 *cell_mid;
     const unsigned *cell_key;
-    const int *nbr;
+    const int *nbr;   // neighbour cell lists, row stride g.noff
+    const int *ncnt;  // (adjacent count << 16) | count
 };
 
 // Count pass (Section IV-B, fused pair test + count).  Per cell A:
 //   |A| >= min_pts and no exact counts: every point is core, no pair test;
 //   |A| >= 32 with exact counts: one lane per point, candidates broadcast;
-//   otherwise: per point, the warp walks the flattened candidates, 128 per
-//   step with four independent loads per lane, and stops once the count
-//   reaches min_pts (unless exact counts are asked for).
+//   otherwise (|A| < 32): the warp walks the flattened candidates, 128 per
+//   step with four independent loads per lane, and tests each step against
+//   every point of A that is still below min_pts (all of them with exact
+//   counts).
 // Then the smallest core index of A goes to cell_rep[A], and every core point
 // of A is hung under it in the union-find forest (cells are cliques); other
-// points are their own parent.
+// points are their own parent.  cell_mid[A] gets a core point of A near its
+// centre (among its first 128 points), which the merge pass tries first.
 template <int D>
-__global__ void __launch_bounds__(256) grid_count_kernel(PairArgs a, int min_pts, int exact, uint8_t *score,
-                                                         int *cell_rep, int *parent, int *counts_out,
-                                                         uint8_t *core_out) {
+__global__ void __launch_bounds__(256, 6) grid_count_kernel(PairArgs a, int min_pts, int exact, uint8_t *score,
+                                                         int *cell_rep, float4 *cell_mid, int *parent,
+                                                         int *counts_out, uint8_t *core_out) {
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
     const int ncells = (int)(*a.ctr0 >> 32);
@@ -276,6 +346,7 @@ __global__ void __launch_bounds__(256) grid_count_kernel(PairArgs a, int min_pts
     for (int A = warp; A < ncells; A += nwarps) {
         const int sA = a.cell_start[A], cA = a.cell_count[A];
         const int *row = a.nbr + (size_t)A * noff;
+        const int nn = a.ncnt[A] & 0xffff;
         int minorig = DB_NONE;
         if (cA >= lim) {
             for (int i0 = lane; i0 < cA; i0 += 128) {
@@ -298,10 +369,9 @@ __global__ void __launch_bounds__(256) grid_count_kernel(PairArgs a, int min_pts
                 const float4 pt = a.spts[p];
                 const float cp = a.g.Tp1 + pt.w, px2 = 2.f * pt.x, py2 = 2.f * pt.y, pz2 = 2.f * pt.z;
                 int cnt = cA;
-                for (int o = 0; o < noff; ++o) {
+                for (int k = 0; k < nn; ++k) {
                     if (__all_sync(FULL, cnt >= lim || !v)) break;
-                    const int B = row[o];
-                    if (B < 0) continue;
+                    const int B = row[k];
                     const int s = a.cell_start[B], e = s + a.cell_count[B];
                     for (int q = s; q < e; ++q) cnt += is_nbr<D>(cp, px2, py2, pz2, a.spts[q]);
                 }
@@ -315,52 +385,58 @@ __global__ void __launch_bounds__(256) grid_count_kernel(PairArgs a, int min_pts
                 }
             }
         } else {
-            // neighbour cells of A, 32 per chunk; the first chunk stays in registers
-            const int B0 = lane < noff ? row[lane] : -1;
-            const int s0 = B0 >= 0 ? a.cell_start[B0] : 0, c0 = B0 >= 0 ? a.cell_count[B0] : 0;
-            const int incl0 = warp_incl_scan(c0), total0 = __shfl_sync(FULL, incl0, 31);
-            for (int i = 0; i < cA; ++i) {
-                const int p = sA + i;
-                const float4 pt = a.spts[p];
-                const float cp = a.g.Tp1 + pt.w, px2 = 2.f * pt.x, py2 = 2.f * pt.y, pz2 = 2.f * pt.z;
-                int cnt = cA;
-                for (int o0 = 0; o0 < noff && cnt < lim; o0 += 32) {
-                    int s = s0, c = c0, incl = incl0, total = total0;
-                    if (o0) {
-                        const int B = (o0 + lane < noff) ? row[o0 + lane] : -1;
-                        s = B >= 0 ? a.cell_start[B] : 0;
-                        c = B >= 0 ? a.cell_count[B] : 0;
-                        incl = warp_incl_scan(c);
-                        total = __shfl_sync(FULL, incl, 31);
-                    }
-                    for (int base = 0; base < total && cnt < lim; base += 128) {
-                        float4 qq[4];
-                        bool val[4];
+            // |A| < 32: lane i owns point i of A.  Each chunk of candidates is
+            // loaded once and tested against every point still below the limit.
+            const bool mine = lane < cA;
+            const float4 pt = a.spts[sA + (mine ? lane : 0)];
+            const float cpm = a.g.Tp1 + pt.w, px2m = 2.f * pt.x, py2m = 2.f * pt.y, pz2m = 2.f * pt.z;
+            int cnt = cA;
+            unsigned pend = __ballot_sync(FULL, mine);  // cA < lim here
+            for (int k0 = 0; k0 < nn && pend; k0 += 32) {
+                const int B = (k0 + lane < nn) ? row[k0 + lane] : -1;
+                const int s = B >= 0 ? a.cell_start[B] : 0, c = B >= 0 ? a.cell_count[B] : 0;
+                const int incl = warp_incl_scan(c), total = __shfl_sync(FULL, incl, 31);
+                for (int base = 0; base < total && pend; base += 128) {
+                    float4 qq[4];
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int j = base + 32 * u + lane;
-                            const int q = locate(j, incl, c, s);
-                            val[u] = j < total;
-                            qq[u] = val[u] ? a.spts[q] : make_float4(0.f, 0.f, 0.f, -1e30f);
-                        }
-#pragma unroll
-                        for (int u = 0; u < 4; ++u)
-                            cnt += __popc(__ballot_sync(FULL, val[u] && is_nbr<D>(cp, px2, py2, pz2, qq[u])));
+                    for (int u = 0; u < 4; ++u) {
+                        const int j = base + 32 * u + lane;
+                        const int q = locate(j, incl, c, s);
+                        qq[u] = j < total ? a.spts[q] : make_float4(0.f, 0.f, 0.f, -1e30f);
                     }
+                    for (unsigned m = pend; m; m &= m - 1) {
+                        const int i = __ffs(m) - 1;
+                        const float cp = __shfl_sync(FULL, cpm, i), px2 = __shfl_sync(FULL, px2m, i);
+                        const float py2 = D > 1 ? __shfl_sync(FULL, py2m, i) : 0.f;
+                        const float pz2 = D > 2 ? __shfl_sync(FULL, pz2m, i) : 0.f;
+                        int add = 0;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) add += is_nbr<D>(cp, px2, py2, pz2, qq[u]);
+                        const int r = (int)__reduce_add_sync(FULL, (unsigned)add);
+                        if (lane == i) cnt += r;
+                    }
+                    pend = __ballot_sync(FULL, mine && cnt < lim);
                 }
+            }
+            if (mine) {
+                const int p = sA + lane;
                 const bool core = cnt >= min_pts;
-                if (lane == 0) {
-                    const int o = a.sidx[p];
-                    score[p] = core;
-                    if (counts_out) counts_out[o] = cnt;
-                    if (core_out) core_out[o] = core;
-                }
-                if (core) minorig = min(minorig, a.sidx[p]);
+                const int o = a.sidx[p];
+                score[p] = core;
+                if (counts_out) counts_out[o] = cnt;
+                if (core_out) core_out[o] = core;
+                if (core) minorig = min(minorig, o);
             }
         }
         minorig = warp_min(minorig);
         if (lane == 0) cell_rep[A] = minorig;
         __syncwarp();
+        // A's centre in doubled grid units, for the core point nearest to it
+        const unsigned key = a.cell_key[A];
+        const int G = a.g.G, cc = a.g.c;
+        const int cx2 = 2 * (int)(key % G) * cc + cc - 1, cy2 = 2 * (int)((key / G) % G) * cc + cc - 1,
+                  cz2 = 2 * (int)(key / ((unsigned)G * G)) * cc + cc - 1;
+        unsigned long long near = ~0ull;  // (squared distance to the centre << 32) | position
         for (int i0 = lane; i0 < cA; i0 += 128) {
             int o[4];
             uint8_t sc[4];
@@ -373,20 +449,43 @@ __global__ void __launch_bounds__(256) grid_count_kernel(PairArgs a, int min_pts
 #pragma unroll
             for (int u = 0; u < 4; ++u)
                 if (i0 + 32 * u < cA) parent[o[u]] = sc[u] ? minorig : o[u];
+            if (i0 < 32) {  // among the first 128 points only
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (sc[u]) {
+                        const float4 q = a.spts[sA + i0 + 32 * u];
+                        const int dx = 2 * (int)q.x - cx2, dy = D > 1 ? 2 * (int)q.y - cy2 : 0,
+                                  dz = D > 2 ? 2 * (int)q.z - cz2 : 0;
+                        const unsigned long long k =
+                            ((unsigned long long)(unsigned)(dx * dx + dy * dy + dz * dz) << 32) | (unsigned)(i0 + 32 * u);
+                        near = k < near ? k : near;
+                    }
+            }
+        }
+        if (minorig != DB_NONE) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long y = __shfl_xor_sync(FULL, near, o);
+                near = y < near ? y : near;
+            }
+            if (lane == 0) cell_mid[A] = a.spts[sA + (int)(near & 0xffffffffull)];
         }
     }
 }
 
 // Merge pass (Section IV-C).  The core points of one cell are already one set
 // (cells are cliques).  Lanes look at up to 32 neighbouring cells B of A at
-// once (offsets [o_begin, o_end), each cell pair from its smaller key); for
-// every B with cores that is not yet in A's set, the warp searches for one
-// core pair within eps and unites the two sets at the first hit.  The search
+// once (the adjacent part of A's neighbour list in one launch, the outer ring
+// in a second; each cell pair from its smaller key).  In the adjacent launch,
+// a lane whose two central core points (cell_mid) are within eps unites the
+// two sets at once; for every other B with cores that is not yet in A's set,
+// the warp searches for one core pair within eps and unites the two sets at
+// the first hit.  The search
 // stages up to 128 points of the smaller cell in the warp's shared memory
 // (coalesced loads) and runs the lanes over the larger cell against them.
 template <int D>
 __global__ void __launch_bounds__(256) grid_union_kernel(PairArgs a, const uint8_t *__restrict__ score, int *parent,
-                                                         unsigned *status, int o_begin, int o_end) {
+                                                         unsigned *status, bool far_ring) {
     __shared__ float4 ybuf[8][128];
     __shared__ uint8_t ycore[8][128];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -400,12 +499,22 @@ __global__ void __launch_bounds__(256) grid_union_kernel(PairArgs a, const uint8
         const unsigned keyA = a.cell_key[A];
         const int sA = a.cell_start[A], cA = a.cell_count[A];
         const int *row = a.nbr + (size_t)A * a.g.noff;
-        for (int o0 = o_begin; o0 < o_end; o0 += 32) {
-            const int o = o0 + lane;
-            const int B = o < o_end ? row[o] : -1;
+        const int nc = a.ncnt[A];
+        const int k_begin = far_ring ? (nc >> 16) : 0, k_end = far_ring ? (nc & 0xffff) : (nc >> 16);
+        const bool use_mid = !far_ring;
+        const float4 mA = use_mid ? a.cell_mid[A] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float cmA = a.g.Tp1 + mA.w, mx2 = 2.f * mA.x, my2 = 2.f * mA.y, mz2 = 2.f * mA.z;
+        for (int k0 = k_begin; k0 < k_end; k0 += 32) {
+            const int k = k0 + lane;
+            const int B = k < k_end ? row[k] : -1;
             const int repB = (B >= 0 && a.cell_key[B] > keyA) ? a.cell_rep[B] : DB_NONE;
+            const float4 mB = (use_mid && repB != DB_NONE) ? a.cell_mid[B] : make_float4(0.f, 0.f, 0.f, -1e30f);
             bool need = repB != DB_NONE;
             if (need) need = db::uf_find(parent, repA) != db::uf_find(parent, repB);
+            // the two central core points first: a hit unites at once, lanes in parallel
+            const bool hit = need && use_mid && is_nbr<D>(cmA, mx2, my2, mz2, mB);
+            if (hit) db::uf_unite(parent, repA, repB, status);
+            need = need && !hit;
             unsigned todo = __ballot_sync(FULL, need);
             bool first = true;
             while (todo) {
@@ -460,8 +569,9 @@ __global__ void __launch_bounds__(256) grid_union_kernel(PairArgs a, const uint8
 // (the reading used for points reachable from several clusters).  Only cells
 // with fewer than min_pts points hold non-core points.  The own cell's
 // representative is a neighbour (cliques); other cells are skipped when their
-// representative (their smallest core index) cannot beat the current best.
-// Candidates are walked 128 per step, four independent loads per lane.
+// representative (their smallest core index) cannot beat the current best of
+// any point.  Candidates are walked 128 per step, four independent loads per
+// lane, and each step is tested against every non-core point of A.
 template <int D>
 __global__ void __launch_bounds__(256) grid_border_kernel(PairArgs a, int min_pts, const uint8_t *__restrict__ score,
                                                           int *__restrict__ bord) {
@@ -471,52 +581,56 @@ __global__ void __launch_bounds__(256) grid_border_kernel(PairArgs a, int min_pt
     const int noff = a.g.noff;
     for (int A = warp; A < ncells; A += nwarps) {
         const int sA = a.cell_start[A], cA = a.cell_count[A];
-        if (cA >= min_pts) continue;
-        bool nc = false;  // any non-core point here?
-        for (int i = lane; i < cA; i += 32) nc |= !score[sA + i];
-        if (!__any_sync(FULL, nc)) continue;
+        if (cA >= min_pts) continue;  // all core
         const int repA = a.cell_rep[A];
         const int *row = a.nbr + (size_t)A * noff;
-        const int B0 = lane < noff ? row[lane] : -1;
-        const int r0 = B0 >= 0 ? a.cell_rep[B0] : DB_NONE;
-        const int s0 = B0 >= 0 ? a.cell_start[B0] : 0, c0 = B0 >= 0 ? a.cell_count[B0] : 0;
-        for (int i = 0; i < cA; ++i) {
-            const int p = sA + i;
-            if (score[p]) continue;
-            const float4 pt = a.spts[p];
-            const float cp = a.g.Tp1 + pt.w, px2 = 2.f * pt.x, py2 = 2.f * pt.y, pz2 = 2.f * pt.z;
-            int b = repA;
-            for (int o0 = 0; o0 < noff; o0 += 32) {
-                int r = r0, s = s0, c = c0;
-                if (o0) {
-                    const int B = (o0 + lane < noff) ? row[o0 + lane] : -1;
-                    r = B >= 0 ? a.cell_rep[B] : DB_NONE;
-                    s = B >= 0 ? a.cell_start[B] : 0;
-                    c = B >= 0 ? a.cell_count[B] : 0;
-                }
-                if (r >= b) c = 0;  // cannot beat b
+        const int nn = a.ncnt[A] & 0xffff;
+        for (int i0 = 0; i0 < cA; i0 += 32) {
+            // lane i owns point i0 + i of A when it is not core
+            const int i = i0 + lane;
+            const bool mine = i < cA && !score[sA + i];
+            const unsigned pend = __ballot_sync(FULL, mine);
+            if (!pend) continue;
+            const float4 pt = a.spts[sA + (i < cA ? i : 0)];
+            const float cpm = a.g.Tp1 + pt.w, px2m = 2.f * pt.x, py2m = 2.f * pt.y, pz2m = 2.f * pt.z;
+            int b = repA;  // the own cell's smallest core index (cells are cliques)
+            for (int k0 = 0; k0 < nn; k0 += 32) {
+                const int B = (k0 + lane < nn) ? row[k0 + lane] : -1;
+                const int r = B >= 0 ? a.cell_rep[B] : DB_NONE;
+                const int s = B >= 0 ? a.cell_start[B] : 0;
+                int c = B >= 0 ? a.cell_count[B] : 0;
+                const int bmax = (int)__reduce_max_sync(FULL, mine ? (unsigned)b : 0u);
+                if (r >= bmax) c = 0;  // cannot beat any point's current best
                 const int incl = warp_incl_scan(c), total = __shfl_sync(FULL, incl, 31);
-                int best = b;
                 for (int base = 0; base < total; base += 128) {
                     float4 qq[4];
                     int qi[4];
-                    uint8_t sc[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const int j = base + 32 * u + lane;
                         const int q = locate(j, incl, c, s);
                         const bool v = j < total;
-                        sc[u] = v ? score[q] : 0;
-                        qi[u] = v ? a.sidx[q] : DB_NONE;
+                        const uint8_t scq = v ? score[q] : 0;  // three independent loads
+                        const int qv = v ? a.sidx[q] : DB_NONE;
                         qq[u] = v ? a.spts[q] : make_float4(0.f, 0.f, 0.f, -1e30f);
+                        qi[u] = scq ? qv : DB_NONE;
                     }
+                    for (unsigned m = pend; m; m &= m - 1) {
+                        const int k = __ffs(m) - 1;
+                        const float cp = __shfl_sync(FULL, cpm, k), px2 = __shfl_sync(FULL, px2m, k);
+                        const float py2 = D > 1 ? __shfl_sync(FULL, py2m, k) : 0.f;
+                        const float pz2 = D > 2 ? __shfl_sync(FULL, pz2m, k) : 0.f;
+                        const int bk = __shfl_sync(FULL, b, k);
+                        int best = bk;
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (sc[u] && qi[u] < best && is_nbr<D>(cp, px2, py2, pz2, qq[u])) best = qi[u];
+                        for (int u = 0; u < 4; ++u)
+                            if (qi[u] < best && is_nbr<D>(cp, px2, py2, pz2, qq[u])) best = qi[u];
+                        best = (int)__reduce_min_sync(FULL, (unsigned)best);
+                        if (lane == k) b = best;
+                    }
                 }
-                b = warp_min(best);
             }
-            if (lane == 0) bord[p] = b;
+            if (mine) bord[sA + i] = b;
         }
     }
 }
@@ -590,17 +704,16 @@ __global__ void grid_label_kernel(int n, const int *__restrict__ sidx, const int
 }
 
 __global__ void grid_candidates_kernel(GridGeom g, const unsigned long long *ctr0, const int *__restrict__ cell_count,
-                                       const int *__restrict__ nbr, unsigned long long *out) {
+                                       const int *__restrict__ nbr, const int *__restrict__ ncnt,
+                                       unsigned long long *out) {
     __shared__ unsigned long long red[32];
     const int ncells = (int)(*ctr0 >> 32);
     unsigned long long s = 0;
     for (int A = blockIdx.x * blockDim.x + threadIdx.x; A < ncells; A += gridDim.x * blockDim.x) {
         const long long ca = cell_count[A];
         long long t = ca;
-        for (int o = 0; o < g.noff; ++o) {
-            const int B = nbr[(size_t)A * g.noff + o];
-            if (B >= 0) t += cell_count[B];
-        }
+        const int nn = ncnt[A] & 0xffff;
+        for (int k = 0; k < nn; ++k) t += cell_count[nbr[(size_t)A * g.noff + k]];
         s += (unsigned long long)(ca * t);
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -621,22 +734,42 @@ int64_t isqrt64(int64_t v) {
     return r;
 }
 
+// Fork: work enqueued on the returned stream may run beside later work on st
+// (the side stream, except while per-kernel marks are taken); join: st waits
+// for it.
+cudaStream_t fork(const DbWork &w, cudaStream_t st, int k) {
+    if (!w.side || w.marks->on) return st;
+    cudaEventRecord(w.fj[k], st);
+    cudaStreamWaitEvent(w.side, w.fj[k], 0);
+    return w.side;
+}
+
+void join(const DbWork &w, cudaStream_t st, cudaStream_t s2, int k) {
+    if (s2 == st) return;
+    cudaEventRecord(w.fj[k], s2);
+    cudaStreamWaitEvent(st, w.fj[k], 0);
+}
+
 template <int D>
 cudaError_t grid_pair_passes(const DbWork &w, const GridGeom &g, int n, int min_pts, bool exact, int32_t *labels,
                              int32_t *counts_out, uint8_t *core_out, cudaStream_t st) {
-    PairArgs a{g, w.ctr, w.spts, w.sidx, w.cell_start, w.cell_count, w.cell_rep, w.cell_key, w.nbr};
+    PairArgs a{g,          w.ctr,      w.spts,     w.sidx, w.cell_start, w.cell_count,
+               w.cell_rep, w.cell_mid, w.cell_key, w.nbr,  w.ncnt};
     const int wgrid = 152 * 16;  // 8 warps per block, warps stride over the cells
-    grid_count_kernel<D><<<wgrid, 256, 0, st>>>(a, min_pts, exact ? 1 : 0, w.score, w.cell_rep, w.parent,
-                                                counts_out, core_out);
+    grid_count_kernel<D><<<wgrid, 256, 0, st>>>(a, min_pts, exact ? 1 : 0, w.score, w.cell_rep, w.cell_mid,
+                                                w.parent, counts_out, core_out);
     w.marks->kernel("grid_count", st);
-    grid_union_kernel<D><<<wgrid, 256, 0, st>>>(a, w.score, w.parent, w.status, 0, g.nnear);
+    // The border pass needs the core flags but not the merge: it runs beside it.
+    cudaStream_t s2 = fork(w, st, 2);
+    grid_border_kernel<D><<<wgrid, 256, 0, s2>>>(a, min_pts, w.score, w.border);
+    w.marks->kernel("grid_border", s2);
+    grid_union_kernel<D><<<wgrid, 256, 0, st>>>(a, w.score, w.parent, w.status, false);
     w.marks->kernel("grid_union_near", st);
     if (g.noff > g.nnear) {
-        grid_union_kernel<D><<<wgrid, 256, 0, st>>>(a, w.score, w.parent, w.status, g.nnear, g.noff);
+        grid_union_kernel<D><<<wgrid, 256, 0, st>>>(a, w.score, w.parent, w.status, true);
         w.marks->kernel("grid_union_far", st);
     }
-    grid_border_kernel<D><<<wgrid, 256, 0, st>>>(a, min_pts, w.score, w.border);
-    w.marks->kernel("grid_border", st);
+    join(w, st, s2, 3);
     // the hash cursors are free after the scatter: they hold the cell roots
     grid_cell_root_kernel<<<152 * 4, 256, 0, st>>>(w.ctr, w.cell_rep, w.parent, w.hcursor, w.ctr);
     w.marks->kernel("grid_cell_root", st);
@@ -698,17 +831,26 @@ cudaError_t launch_grid_path(const DbWork &w, const GridGeom &g, const float *x,
     cudaError_t e;
     if ((e = cudaMemsetAsync(w.hkey, 0xff, sizeof(unsigned) * H, st))) return e;
     if ((e = cudaMemsetAsync(w.hcount, 0, sizeof(int) * H, st))) return e;
+    // occupancy bitmap of all G^d cells, when it fits its buffer
+    int64_t all_cells = 1;
+    for (int k = 0; k < g.d; ++k) all_cells *= g.G;
+    const int64_t occ_words = (all_cells + 31) / 32;
+    unsigned *occ = occ_words <= w.occ_cap ? w.occ : nullptr;
+    if (occ && (e = cudaMemsetAsync(occ, 0, sizeof(unsigned) * occ_words, st))) return e;
     const int nb = (n + 255) / 256;
     grid_prep_kernel<<<nb, 256, 0, st>>>(x, n, g, w.hkey, w.hcount, w.slot_of, w.pts4, w.status);
     w.marks->kernel("grid_prep", st);
     const int cells_per_block = 256 * CELLS_PER_THREAD;
     grid_cells_kernel<<<(unsigned)((H + cells_per_block - 1) / cells_per_block), 256, 0, st>>>(
-        (int)H, w.hkey, w.hcount, w.hval, w.hcursor, w.cell_start, w.cell_count, w.cell_key, w.cell_rep, w.ctr);
+        (int)H, w.hkey, w.hcount, w.hpack, w.hcursor, w.cell_start, w.cell_count, w.cell_key, w.cell_rep, occ, w.ctr);
     w.marks->kernel("grid_cells", st);
-    grid_scatter_kernel<<<nb, 256, 0, st>>>(n, w.slot_of, w.hcursor, w.hval, w.pts4, w.spts, w.sidx, w.scell);
+    // The neighbour lists need the cell table but not the grouped points.
+    cudaStream_t s2 = fork(w, st, 0);
+    grid_nbr_kernel<<<152 * 16, 256, 0, s2>>>(g, w.ctr, w.cell_key, w.hpack, occ, w.nbr, w.ncnt);
+    w.marks->kernel("grid_nbrs", s2);
+    grid_scatter_kernel<<<nb, 256, 0, st>>>(n, w.slot_of, w.hcursor, w.hpack, w.pts4, w.spts, w.sidx, w.scell);
     w.marks->kernel("grid_scatter", st);
-    grid_nbr_kernel<<<152 * 8, 256, 0, st>>>(g, w.ctr, w.cell_key, w.hkey, w.hval, w.nbr);
-    w.marks->kernel("grid_nbrs", st);
+    join(w, st, s2, 1);
     if ((e = cudaGetLastError())) return e;
     switch (g.d) {
         case 1: return grid_pair_passes<1>(w, g, n, min_pts, exact, labels, counts_out, core_out, st);
@@ -718,7 +860,7 @@ cudaError_t launch_grid_path(const DbWork &w, const GridGeom &g, const float *x,
 }
 
 cudaError_t launch_grid_candidates(const DbWork &w, const GridGeom &g, int64_t /*n*/, cudaStream_t st) {
-    grid_candidates_kernel<<<152 * 4, 256, 0, st>>>(g, w.ctr, w.cell_count, w.nbr, w.ctr + 1);
+    grid_candidates_kernel<<<152 * 4, 256, 0, st>>>(g, w.ctr, w.cell_count, w.nbr, w.ncnt, w.ctr + 1);
     w.marks->kernel("grid_candidates", st);
     return cudaGetLastError();
 }

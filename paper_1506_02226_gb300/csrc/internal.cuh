@@ -152,7 +152,9 @@ struct DbWork {
     int32_t hbits;
     uint32_t *hkey;
     int32_t *hcount;
-    int32_t *hval;
+    int2 *hpack;            // cell hash: {key, cell id} (written after the inserts) [hcap]
+    uint32_t *occ;          // occupancy bitmap of all G^d cells, when it fits [occ_cap]
+    int64_t occ_cap;        // words (128 bits per point, at least 2^20 bits)
     int32_t *hcursor;
     int32_t *slot_of;       // hash slot of each point [cap_n]
     float4 *pts4;           // {u0,u1,u2,-|u|^2} by point index [cap_n]
@@ -161,8 +163,10 @@ struct DbWork {
     int32_t *scell;         // cell id of each grouped position [cap_n]
     uint8_t *score;         // core flag of each grouped position [cap_n]
     int32_t *cell_start, *cell_count, *cell_rep;  // [cap_n]
+    float4 *cell_mid;       // a core point near each cell's centre [cap_n]
     uint32_t *cell_key;     // [cap_n]
-    int32_t *nbr;           // neighbour-cell table [cap_n * noff_cap]
+    int32_t *nbr;           // neighbour cell lists, adjacent first [cap_n * noff_cap]
+    int32_t *ncnt;          // (adjacent count << 16) | count [cap_n]
     int32_t noff_cap;
     // tensor-core path (max_d >= 16)
     int64_t tc_cap_pad;     // rows of each packed operand (cap_n rounded up to 256)
@@ -176,6 +180,10 @@ struct DbWork {
     int32_t *edges_used;    // per CTA
     int64_t edge_cap;       // total edge slots
     PhaseMarks *marks;      // host-side timing marks of the owning plan
+    // second stream of the grid path: independent kernels run beside each
+    // other (fork/join by events); unused while per-kernel marks are taken
+    cudaStream_t side;
+    cudaEvent_t fj[4];
 };
 
 // Host-side grid geometry for d <= 3 (see grid.cu).

@@ -25,11 +25,13 @@ pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "hand_cases.json")
 
 
-def gpu_detail(points, eps, min_pts, grid=B.DBSCAN_GRID_AUTO, label_mode=0, precision=B.DBSCAN_PREC_AUTO):
+def gpu_detail(points, eps, min_pts, grid=B.DBSCAN_GRID_AUTO, label_mode=0, precision=B.DBSCAN_PREC_AUTO,
+               max_n=None):
     from paper_1506_02226_gb300.api import Plan
     n, d = points.shape
     x = torch.from_numpy(np.ascontiguousarray(points, dtype=np.float32)).cuda()
-    with Plan(max_n=max(n, 1), max_d=max(d, 1), grid=grid, label_mode=label_mode, precision=precision) as p:
+    with Plan(max_n=max(n, 1, max_n or 0), max_d=max(d, 1), grid=grid, label_mode=label_mode,
+              precision=precision) as p:
         lab, cnt, core, st = p.run_detail(x, eps, min_pts)
     return lab.cpu().numpy(), cnt.cpu().numpy(), core.cpu().numpy().astype(bool), st
 
@@ -60,6 +62,20 @@ def assert_matches_oracle(points, eps, min_pts, grids=None):
             assert st["n_core"] + st["n_border"] + st["n_noise"] == n
             assert st["n_core"] == int(want_core.sum())
             assert st["n_clusters"] == len(set(want_lab[want_lab >= 0].tolist()))
+
+
+def test_grid_occupancy_bitmap_both_ways():
+    """3-D neighbour lists with and without the occupancy bitmap (it is used when
+    all G^3 cell bits fit the plan's buffer: 128 bits per point of max_n)."""
+    x = _blobs(77, 3000, 3, spread=14)
+    for eps, max_n in ((6 / 1024, 3000), (6 / 1024, 200_000), (40 / 1024, 3000)):
+        for mode in (0, 1):
+            want_lab, want_cnt, want_core = oracle.dbscan(x, eps, 5, label_mode=mode)
+            lab, cnt, core, st = gpu_detail(x, eps, 5, grid=B.DBSCAN_GRID_ON, label_mode=mode, max_n=max_n)
+            assert st["path"] == B.DBSCAN_PATH_GRID
+            np.testing.assert_array_equal(cnt, want_cnt)
+            np.testing.assert_array_equal(core, want_core)
+            np.testing.assert_array_equal(lab, want_lab, err_msg=f"eps={eps} max_n={max_n} mode={mode}")
 
 
 # ---------------------------------------------------------------- hand-worked
