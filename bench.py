@@ -55,20 +55,20 @@ def work_units(points: np.ndarray, eps: float, d: int) -> int:
 
 
 # ------------------------------------------------------------------ work units
-def grid_candidate_pairs(points: np.ndarray, eps: float) -> int:
-    """Ordered candidate pairs of the eps-grid (host-side count, numpy).
+def grid_structure(points: np.ndarray, eps: float) -> dict:
+    """The eps-grid of an instance, counted on the host with numpy.
 
     Cell side c = floor(sqrt(floor(T/d))) + 1 grid units; a point's candidates
-    are the points of its own cell and of every cell offset o with
-    sum_k [o_k != 0]((|o_k|-1)c+1)^2 <= T.
+    are the points of its own cell and of every occupied cell at an offset o
+    with sum_k [o_k != 0]((|o_k|-1)c+1)^2 <= T.  Returns the ordered candidate
+    pairs, the occupied cells and the neighbour-list entries (occupied cells at
+    kept offsets, adjacent |o_k| <= 1 and outer ring separately).
     """
     u = np.rint(points.astype(np.float64) * 1024).astype(np.int64)
     n, d = u.shape
     e = float(np.float32(eps))
     T = min(math.floor(e * e * 1048576.0), d * 1023 * 1023)
-    c = math.isqrt(T // d) + 1
-    s = math.isqrt(T)
-    r = -(-s // c)
+    c, offs = grid_offsets(d, T)
     G = -(-1024 // c)
     cells = u // c
     key = np.zeros(n, np.int64)
@@ -77,21 +77,27 @@ def grid_candidate_pairs(points: np.ndarray, eps: float) -> int:
     uk, cnt = np.unique(key, return_counts=True)
     coords = np.stack([(uk // G ** k) % G for k in range(d)], axis=1)
     total = np.zeros(len(uk), np.int64)
-    import itertools
-    for off in itertools.product(range(-r, r + 1), repeat=d):
-        md = sum(((abs(o) - 1) * c + 1) ** 2 for o in off if o)
-        if md > T:
-            continue
+    near = far = 0
+    for off in offs:
         nc = coords + np.array(off)
         ok = np.all((nc >= 0) & (nc < G), axis=1)
         nk = np.zeros(len(uk), np.int64)
         for k in reversed(range(d)):
             nk = nk * G + nc[:, k]
-        pos = np.searchsorted(uk, nk)
-        pos = np.clip(pos, 0, len(uk) - 1)
+        pos = np.clip(np.searchsorted(uk, nk), 0, len(uk) - 1)
         hit = ok & (uk[pos] == nk)
         total += np.where(hit, cnt[pos], 0)
-    return int((cnt * total).sum())
+        if max(abs(x) for x in off) <= 1:
+            near += int(hit.sum())
+        else:
+            far += int(hit.sum())
+    return {"candidate_pairs": int((cnt * (cnt + total)).sum()), "cells": len(uk), "near_entries": near,
+            "far_entries": far}
+
+
+def grid_candidate_pairs(points: np.ndarray, eps: float) -> int:
+    """Ordered candidate pairs of the eps-grid (host-side count, numpy)."""
+    return grid_structure(points, eps)["candidate_pairs"]
 
 
 # ------------------------------------------------------------------ clocks
@@ -157,7 +163,8 @@ def grid_offsets(d: int, T: int):
 # source means the counters no longer describe the kernel, and the bench line
 # reports traffic null.
 NCU_TRAFFIC = {
-    ("lowd2", "grid_border"): (8189440, "paper_1506_02226_gb300/csrc/grid.cu", "0e88609cded5"),
+    ("lowd2", "grid_count"): (12894464, "paper_1506_02226_gb300/csrc/grid.cu", "3f15e8f0d907"),
+    ("lowd3", "grid_count"): (30360064, "paper_1506_02226_gb300/csrc/grid.cu", "3f15e8f0d907"),
 }
 
 
@@ -175,42 +182,45 @@ def ncu_traffic(workload: str, kernel: str):
     return nbytes if cur.startswith(sha) else None
 
 
-def algorithmic_work(name: str, n: int, d: int, eps: float, st: dict):
-    """(bound, bytes per launch) of a kernel: the bytes it has to move at least,
-    counting every input it must read and every output it must write once.
+def algorithmic_work(name: str, n: int, d: int, gs: dict | None):
+    """(bound, bytes per launch) of a grid kernel: the bytes it has to move at
+    least, counting every input it must read and every output it must write
+    once.  gs is the instance's grid_structure (cells C, neighbour-list entries
+    E = adjacent En + outer Ef; H hash slots).
 
-    Grid kernels (per point unless marked): prep reads x (4d) and writes the
-    packed point (16) and hash slot (4), touching one hash entry (8); cells reads
-    the hash table (8 per slot) and writes 24 per cell; scatter reads slot,
-    cursor, cell id and packed point (28) and writes packed point, index and
-    cell id (24); nbrs reads a cell key (4) and a hash entry (8) and writes a
-    table entry (4) per (cell, offset); count reads index (4), writes core flag
-    (1) and parent (4), plus 12 per cell and its table row (4 per offset);
-    union reads per cell 16 bytes and its table row, plus 16 per neighbouring
-    cell; border reads the index and flag of non-core points' cells; root reads a
-    cell's representative and parent chain and writes its root (16 per cell);
-    label reads index, cell, flag, cell root and border (17) and writes the label.
+      prep     reads x (4d), writes packed point (16) and hash slot (4), one
+               hash entry (8)                                 (4d + 28) n
+      cells    reads key and count of every slot (8), writes the packed
+               {key, id} table (8), 24 per cell               16 H + 24 C
+      scatter  reads slot, cell id and packed point (24), writes packed
+               point, index and cell id (24), one cursor (4)  52 n
+      nbrs     per cell key and list length (8), per entry a hash entry (8)
+               and the list entry (4)                         8 C + 12 E
+      count    per point the packed point (16), index (4), core flag and
+               parent written (5); per cell 32 (range, length, rep, centre);
+               per entry list entry and neighbour range (12)  25 n + 32 C + 12 E
+      union    per cell 32; per adjacent entry list entry, key, rep and
+               centre point (28); per outer entry 12           32 C + 28 En / 12 Ef
+      border   per point core flag (1) and border written (4) 5 n
+      root     per cell rep, parent and root (16)             16 C
+      label    per point index, cell, flag, cell root, border (17), label (4)  21 n
     """
-    e = float(np.float32(eps))
-    T = min(math.floor(e * e * 1048576.0), d * 1023 * 1023)
-    cells = max(int(st.get("cells", 0)), 1)
+    if d > 3 or gs is None:
+        return None, 0
+    C, En, Ef = gs["cells"], gs["near_entries"], gs["far_entries"]
+    E = En + Ef
     H = 1 << max(10, math.ceil(math.log2(2 * n)))
-    if d <= 3:
-        _, offs = grid_offsets(d, T)
-        noff = len(offs)
-    else:
-        noff = 0
     table = {
         "grid_prep": (4 * d + 28) * n,
-        "grid_cells": 8 * H + 24 * cells,
+        "grid_cells": 16 * H + 24 * C,
         "grid_scatter": 52 * n,
-        "grid_nbrs": 16 * cells * noff,
-        "grid_count": 9 * n + (12 + 4 * noff) * cells,
-        "grid_union_near": (16 + 4 * noff + 16 * noff) * cells,
-        "grid_union_far": (16 + 4 * noff + 16 * noff) * cells,
+        "grid_nbrs": 8 * C + 12 * E,
+        "grid_count": 25 * n + 32 * C + 12 * E,
+        "grid_union_near": 32 * C + 28 * En,
+        "grid_union_far": 32 * C + 12 * Ef,
         "grid_border": 5 * n,
-        "grid_cell_root": 16 * cells,
-        "grid_label": 17 * n,
+        "grid_cell_root": 16 * C,
+        "grid_label": 21 * n,
     }
     if name in table:
         return "hbm", table[name]
@@ -548,8 +558,10 @@ def run_ours(args, wl_name):
     with Plan(max_n=n, max_d=d, precision=prec) as p:
         _, st0 = p.run(x, inst.eps, inst.min_pts, stats=True)
     units = st0["candidate_pairs"]
+    gs = None
     if st0["path"] == B.DBSCAN_PATH_GRID:
-        host_units = grid_candidate_pairs(inst.points, inst.eps)
+        gs = grid_structure(inst.points, inst.eps)
+        host_units = gs["candidate_pairs"]
         if host_units != units:
             raise RuntimeError(f"candidate-pair count mismatch: device {units} host {host_units}")
 
@@ -626,7 +638,7 @@ def run_ours(args, wl_name):
     avg = {k: statistics.mean(v) for k, v in kern.items()}
     dom = max(avg, key=avg.get)
     peaks = load_peaks()
-    bound, work = algorithmic_work(dom, n, d, inst.eps, st0)
+    bound, work = algorithmic_work(dom, n, d, gs)
     if dom.startswith("tc_") and dom in ("tc_count", "tc_union", "tc_border"):
         K = -(-d // 16) * 16
         nc = st0["n_core"]
