@@ -97,9 +97,6 @@ size_t layout(DbWork &w, const dbscan_opts &o, char *base) {
         w.list_a = c.take<int32_t>(n);
         w.list_b = c.take<int32_t>(n);
         w.tc_lens = c.take<int32_t>(4);
-        w.edge_cap = 16 * n + 4096;
-        w.edges = c.take<int2>((size_t)w.edge_cap);
-        w.edges_used = c.take<int32_t>(1024);
     } else {
         w.tc_cap_pad = 0;
     }

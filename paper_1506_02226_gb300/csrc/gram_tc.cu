@@ -92,9 +92,6 @@ struct TcArgs {
     unsigned *status;
     unsigned long long *ctr;  // [6] band pairs, [7] verify: disagreements outside the band, [8] max |w - exact|
     int col_chunk;            // column tiles per work item
-    int2 *edges;              // union pass: core-core neighbour pairs, cap_per_cta per CTA
-    int *edges_used;          // edges written by each CTA
-    int edge_cap_per_cta;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -265,18 +262,31 @@ struct __align__(16) Smem {
     uint64_t t_full[2], t_empty[2];
     uint32_t tmem_base;
     int abort_flag;
-    int edge_used;
+    // union pass: hints of the column points' sets, per accumulator buffer and
+    // column half (shared by the four warps of a half; a buffer is refilled only
+    // after all eight epilogue warps have released it)
+    int colroot[2][2][128];
 };
 
-// Work item w: column chunk ch = w / nrt and row tile rt = w % nrt, so the
-// CTAs running at one time share their column chunk and its B tiles come from
-// L2; column tiles [c0, c1) of the chunk.
+// Work item w covers row tile rt and column tiles [c0, c1) of one column chunk.
+// Count and border passes: ch = w / nrt, rt = w % nrt, so the CTAs running at
+// one time share their column chunk and its B tiles come from L2.  Merge pass
+// (a.upper): rt = w / nchunk and the chunk rotates with the row tile, so the
+// CTAs running at one time work on different column chunks: the first visit to
+// a chunk's points unites and flattens them, and later visits find them in
+// their cluster's set (the core operand, at most n x 128 bytes, stays in L2).
 __device__ __forceinline__ bool item_range(const TcArgs &a, int w, int nR, int nC, int &rt, int &c0, int &c1) {
     const int nrt = (nR + TM - 1) / TM, nct = (nC + TN - 1) / TN;
     const int nchunk = (nct + a.col_chunk - 1) / a.col_chunk;
     if (w >= nrt * nchunk) return false;
-    const int ch = w / nrt;
-    rt = w - ch * nrt;
+    int ch;
+    if (a.upper) {
+        rt = w / nchunk;
+        ch = (w - rt * nchunk + rt) % nchunk;
+    } else {
+        ch = w / nrt;
+        rt = w - ch * nrt;
+    }
     c0 = ch * a.col_chunk;
     c1 = min(nct, c0 + a.col_chunk);
     if (a.upper) c0 = max(c0, (rt * TM) / TN);  // pairs i < j only: skip tiles left of the diagonal
@@ -293,8 +303,10 @@ __device__ __noinline__ int decide_candidate(float wv, float alpha, float rho_p,
     return (exact_sqdist(v16, K, p, q) <= T ? 1 : 0) | 2;
 }
 
-__device__ __noinline__ void unite_pair(int *parent, int p, int q, unsigned *status) {
-    db::uf_unite(parent, p, q, status);
+// Union of p's and q's sets; returns a root the merged set had at some moment
+// (out of line: keeps the union-find loop out of the epilogue's registers).
+__device__ __noinline__ int unite_root(int *parent, int p, int q, unsigned *status) {
+    return db::uf_unite_root(parent, p, q, status);
 }
 
 
@@ -325,7 +337,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(TcArgs a) {
             mbar_init(&S.b_empty[i], 1 + EPI_WARPS);
         }
         S.abort_flag = 0;
-        S.edge_used = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -439,6 +450,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(TcArgs a) {
             const float alpha = beta_p - (float)a.T;  // |v_p|^2 - T, exact
             const float alo = alpha - (float)FP16_BAND;
             int cnt = 0, bmin = INT_MAX;
+            // union: a member of p's set (its parent, then the last root seen)
+            int rootp = (PASS == TC_UNION && row_ok) ? db::ld_relaxed(a.parent + p) : -2;
             bool ok = true;
             for (int ct = c0; ct < c1; ++ct, ++t) {
                 const int s = t % NSTAGE, b = t & 1;
@@ -449,6 +462,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(TcArgs a) {
                 }
                 tc_fence_after();
                 const MetaBlock &mc = S.metaB[s][half];
+                int *colroot = S.colroot[b][half];
+                bool hints = false;  // union: colroot filled for this tile
 #pragma unroll 1
                 for (int hc = 0; hc < 2; ++hc) {
                     const int cb = hc * 64;  // column within this warp's 128-column half
@@ -523,28 +538,48 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(TcArgs a) {
                     const float thr = BF16 ? alpha : alpha - (float)FP16_BAND;
                     const float mx = fmaxf(fmaxf(fmaxf(wv[0], wv[1]), fmaxf(wv[2], wv[3])),
                                            fmaxf(fmaxf(wv[4], wv[5]), fmaxf(wv[6], wv[7])));
-                    const bool need = row_ok && mx >= thr;
+                    // Border: the columns are core points in ascending index order,
+                    // so a group whose first index is not below the best so far
+                    // cannot improve it.
+                    const bool need = row_ok && mx >= thr && (PASS != TC_BORDER || mc.idx[cb] < bmin);
                     if (!__any_sync(0xffffffffu, need)) continue;
+                    if (PASS == TC_UNION && !hints) {
+                        // parents of this tile's 128 column points, four loads per lane
+                        // (the four warps of the half all write them: any value is a
+                        // member of the column point's set)
+                        int pr[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const int q = mc.idx[lane + 32 * k];
+                            pr[k] = q >= 0 ? db::ld_relaxed(a.parent + q) : -1;
+                        }
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) colroot[lane + 32 * k] = pr[k];
+                        __syncwarp();
+                        hints = true;
+                    }
                     // Rare path: the lanes that need it build the 64-bit mask of
-                    // possible neighbours (for FP16 exactly the neighbours), then
-                    // walk only its set bits.
+                    // possible neighbours (for FP16 exactly the neighbours; padding
+                    // columns never pass, their beta is 1e30).  The merge pass also
+                    // drops the columns whose set hint equals the row's: those pairs
+                    // need no union.
                     uint64_t mask = 0;
                     if (need) {
                         const int col_lim = a.upper ? (i_row - (ct * TN + half * 128)) : -1;  // cols <= this: j <= i
 #pragma unroll
                         for (int j = 0; j < 64; ++j) {
                             const float w1 = fmaf(2.f, __uint_as_float(g[j]), -mc.beta[cb + j]);
-                            const bool c = BF16 ? (fmaf(rho_p, mc.rho[cb + j], w1) >= alpha) : (w1 >= alpha);
+                            bool c = BF16 ? (fmaf(rho_p, mc.rho[cb + j], w1) >= alpha) : (w1 >= alpha);
+                            if (PASS == TC_UNION) c = c && colroot[cb + j] != rootp;
                             mask |= (uint64_t)(c && (cb + j) > col_lim) << j;
                         }
                     }
-                    uint64_t nbm = 0;  // confirmed neighbours among the mask
-                    for (uint64_t mm = mask; mm; mm &= mm - 1) {
-                        const int j = __ffsll((long long)mm) - 1;
-                        const int q = mc.idx[cb + j];
-                        if (q < 0) continue;
-                        bool nb = true;
-                        if (BF16) {
+                    uint64_t nbm = mask;  // confirmed neighbours among the mask
+                    if (BF16) {
+                        nbm = 0;
+                        for (uint64_t mm = mask; mm; mm &= mm - 1) {
+                            const int j = __ffsll((long long)mm) - 1;
+                            const int q = mc.idx[cb + j];
                             // recompute 2G - |v_q|^2 for column j from the accumulator copy in g
                             float gj = 0.f;
 #pragma unroll
@@ -553,31 +588,34 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(TcArgs a) {
                             const float wj = fmaf(2.f, gj, -mc.beta[cb + j]);
                             const int res = decide_candidate<BF16>(wj, alpha, rho_p, mc.rho[cb + j], a.v16, K, p, q, a.T);
                             band_cnt += res >> 1;
-                            nb = res & 1;
+                            if (!(res & 1)) continue;
+                            nbm |= 1ull << j;
+                            if (PASS == TC_BORDER) break;  // ascending columns: the first is the smallest
                         }
-                        if (!nb) continue;
-                        nbm |= 1ull << j;
-                        if (PASS == TC_COUNT) ++cnt;
-                        else if (PASS == TC_BORDER) bmin = min(bmin, q);
                     }
+                    if (PASS == TC_COUNT) cnt += __popcll(nbm);
+                    if (PASS == TC_BORDER && nbm) bmin = min(bmin, mc.idx[cb + __ffsll((long long)nbm) - 1]);
                     if (PASS == TC_UNION) {
-                        // one shared-memory atomic per warp reserves every lane's edges
-                        const int ne = __popcll(nbm);
-                        int incl = ne;
-#pragma unroll
-                        for (int o = 1; o < 32; o <<= 1) {
-                            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                            if (lane >= o) incl += y;
-                        }
-                        const int tot = __shfl_sync(0xffffffffu, incl, 31);
-                        int base = 0;
-                        if (lane == 31 && tot) base = atomicAdd(&S.edge_used, tot);
-                        base = __shfl_sync(0xffffffffu, base, 31) + incl - ne;
-                        int2 *dst = a.edges + (size_t)blockIdx.x * a.edge_cap_per_cta;
-                        for (uint64_t mm = nbm; mm; mm &= mm - 1, ++base) {
-                            const int q = mc.idx[cb + __ffsll((long long)mm) - 1];
-                            if (base < a.edge_cap_per_cta) dst[base] = make_int2(p, q);
-                            else unite_pair(a.parent, p, q, a.status);  // list full: unite here
+                        // Skip a neighbour whose set p is known to be in: colroot[j]
+                        // holds a member of column j's set (its parent, or the root
+                        // of a later union), rootp a member of p's.  Equal members
+                        // mean one set, so only pairs from different-looking sets
+                        // reach the atomics.  After a union both endpoints point
+                        // straight at the returned root (a valid ancestor; never
+                        // written on the root itself, whose link another thread may
+                        // have set), so later tiles find the forest flat and a
+                        // converged cluster costs one shared-memory compare per pair.
+                        for (uint64_t mm = nbm; mm; mm &= mm - 1) {
+                            const int j = cb + __ffsll((long long)mm) - 1;
+                            if (colroot[j] == rootp) continue;
+                            const int q = mc.idx[j];
+                            const int r = unite_root(a.parent, p, q, a.status);
+                            if (r >= 0) {
+                                if (q != r) db::st_relaxed(a.parent + q, r);
+                                if (p != r && r != rootp) db::st_relaxed(a.parent + p, r);
+                            }
+                            rootp = r;
+                            colroot[j] = r;
                         }
                     }
                 }
@@ -623,21 +661,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(TcArgs a) {
         __syncthreads();
     }
     tc_fence_after();
-    if (PASS == TC_UNION && threadIdx.x == 0) a.edges_used[blockIdx.x] = min(S.edge_used, a.edge_cap_per_cta);
     if (warp == 1) tmem_dealloc(tmem, 512);
 }
 
-// Unites the core-core neighbour pairs the union pass listed (one thread per pair).
-__global__ void tc_edges_kernel(const int2 *__restrict__ edges, const int *__restrict__ used, int nctas, int cap,
-                                int *parent, unsigned *status) {
-    const int64_t total = (int64_t)nctas * cap;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(e / cap), k = (int)(e - (int64_t)c * cap);
-        if (k >= used[c]) continue;
-        const int2 pq = edges[e];
-        db::uf_unite(parent, pq.x, pq.y, status);
-    }
-}
 
 // ---------------- preparation kernels ----------------
 
@@ -820,16 +846,8 @@ cudaError_t launch_allpairs_tc(const DbWork &w, const float *x, int64_t n64, int
     a.nR_ptr = a.nC_ptr = lens + 0;
     a.pass = TC_UNION;
     a.upper = 1;
-    a.edges = w.edges;
-    a.edges_used = w.edges_used;
-    a.edge_cap_per_cta = (int)std::min<int64_t>(w.edge_cap / sms, INT_MAX);
-    // CTAs without work items leave their slot untouched: clear every slot so no
-    // edges of an earlier run are replayed.
-    if ((e = cudaMemsetAsync(w.edges_used, 0, sizeof(int) * (size_t)sms, st))) return e;
     if ((e = launch_pass<TC_UNION>(a, sms, st))) return e;
     w.marks->kernel("tc_union", st);
-    tc_edges_kernel<<<152 * 8, 256, 0, st>>>(w.edges, w.edges_used, sms, a.edge_cap_per_cta, w.parent, w.status);
-    w.marks->kernel("tc_union_edges", st);
     // pass 3: non-core x core -> smallest core neighbour
     a.opR = w.opNon;
     a.metaR = reinterpret_cast<const MetaBlock *>(w.metaNon);

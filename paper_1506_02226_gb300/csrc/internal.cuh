@@ -176,9 +176,6 @@ struct DbWork {
     void *metaAll, *metaCore, *metaNon;  // per-point metadata blocks (16 B per row)
     int32_t *list_a, *list_b;  // core / non-core index lists [cap_n]
     int32_t *tc_lens;       // [0] cores, [1] non-cores, [2] all
-    int2 *edges;            // core-core neighbour pairs found by the union pass
-    int32_t *edges_used;    // per CTA
-    int64_t edge_cap;       // total edge slots
     PhaseMarks *marks;      // host-side timing marks of the owning plan
     // second stream of the grid path: independent kernels run beside each
     // other (fork/join by events); unused while per-kernel marks are taken

@@ -267,6 +267,21 @@ def test_tensor_core_path_matches_oracle(name, prec, n, d):
         np.testing.assert_array_equal(lab, want_lab)
 
 
+@pytest.mark.parametrize("name,prec", PRECS)
+def test_tensor_core_dense_neighbourhoods(name, prec):
+    """Almost every point core with hundreds of neighbours, several clusters that
+    touch: the merge pass sees far more neighbour pairs than unions."""
+    n, d = 12_000, 32
+    x = _blobs(4242, n, d, spread=20)
+    eps = float(np.float32(1.6 * 20 * np.sqrt(d) / 1024))
+    want_lab, want_cnt, want_core = oracle.dbscan(x, eps, 8)
+    assert want_core.mean() > 0.9 and np.median(want_cnt) > 50
+    lab, cnt, core, st = gpu_detail(x, eps, 8, grid=B.DBSCAN_GRID_OFF, precision=prec)
+    assert st["path"] == B.DBSCAN_PATH_ALLPAIRS_TC
+    np.testing.assert_array_equal(cnt, want_cnt)
+    np.testing.assert_array_equal(lab, want_lab)
+
+
 @pytest.mark.parametrize("bf16", [0, 1])
 def test_tensor_core_band_holds(bf16):
     """Every pair outside the stated rounding band is decided as exact arithmetic
@@ -315,7 +330,7 @@ def test_full_size_high_d_workload():
 
 def test_tensor_core_plan_reused_across_sizes():
     """One plan, instances of shrinking size: nothing of an earlier run may leak
-    into a later one (per-CTA edge lists, counters, packed operands)."""
+    into a later one (counters, packed operands, set hints)."""
     from paper_1506_02226_gb300.api import Plan
     with Plan(max_n=12_000, max_d=32, precision=B.DBSCAN_PREC_FP16_GRAM, grid=B.DBSCAN_GRID_OFF) as p:
         for seed, n, d in ((1, 11_000, 16), (2, 7519, 16), (3, 3000, 32), (4, 500, 16), (5, 9000, 32)):
