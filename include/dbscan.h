@@ -189,6 +189,18 @@ int dbscan_plan_counters(dbscan_plan *plan, uint64_t *out, int32_t n);
 /* Device bytes the plan's workspace holds. */
 int64_t dbscan_plan_workspace_bytes(const dbscan_plan *plan);
 
+/* Failure-detection test hook (the paper has none).  DBSCAN_HOOK_TC_STALL
+ * makes the plan's next run that takes the tensor-core path issue no MMA in
+ * its counting pass: every bounded device-side wait of that pass then expires
+ * (50 ms budget instead of about 2 s), the CTAs take their abort path (wait
+ * for their own copies, free tensor memory, return), and the run returns
+ * DBSCAN_ERR_TIMEOUT with unspecified labels.  The hook is consumed by that
+ * run; the plan stays usable.  No GPU fault, trap or hang is involved.
+ * Returns DBSCAN_ERR_ARG for a null plan or an unknown hook. */
+#define DBSCAN_HOOK_NONE 0
+#define DBSCAN_HOOK_TC_STALL 1
+int dbscan_plan_test_hook(dbscan_plan *plan, int32_t hook);
+
 /* ---- Batched form: many independent instances in one graph-captured launch sequence ---- */
 
 typedef struct dbscan_instance {

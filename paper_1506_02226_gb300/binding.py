@@ -30,6 +30,7 @@ DBSCAN_PREC_AUTO, DBSCAN_PREC_EXACT_SIMT, DBSCAN_PREC_FP16_GRAM, DBSCAN_PREC_BF1
 DBSCAN_GRID_AUTO, DBSCAN_GRID_ON, DBSCAN_GRID_OFF = 0, 1, 2
 DBSCAN_LABEL_ROOT_INDEX, DBSCAN_LABEL_COMPACT = 0, 1
 DBSCAN_PATH_NONE, DBSCAN_PATH_GRID, DBSCAN_PATH_ALLPAIRS_SIMT, DBSCAN_PATH_ALLPAIRS_TC = 0, 1, 2, 3
+DBSCAN_HOOK_NONE, DBSCAN_HOOK_TC_STALL = 0, 1
 
 c_i32, c_i64, c_f32, c_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_void_p
 
@@ -77,6 +78,7 @@ _SIGS = {
     "dbscan_run_host": (ctypes.c_int, [c_p, c_p, c_i64, c_i32, c_f32, c_i32, c_p, c_p]),
     "dbscan_plan_sync": (ctypes.c_int, [c_p]),
     "dbscan_plan_workspace_bytes": (c_i64, [c_p]),
+    "dbscan_plan_test_hook": (ctypes.c_int, [c_p, c_i32]),
     "dbscan_tc_verify": (ctypes.c_int, [c_p, c_p, c_i64, c_i32, c_f32, c_i32, c_p]),
     "dbscan_plan_counters": (ctypes.c_int, [c_p, c_p, c_i32]),
     "dbscan_plan_phase_times": (ctypes.c_int, [c_p, c_i32, c_p, c_p, c_p]),
@@ -203,6 +205,10 @@ def dbscan_plan_counters(plan: int) -> list[int]:
 
 def dbscan_plan_workspace_bytes(plan: int) -> int:
     return int(lib().dbscan_plan_workspace_bytes(plan))
+
+
+def dbscan_plan_test_hook(plan: int, hook: int) -> None:
+    _check(lib().dbscan_plan_test_hook(plan, hook), "dbscan_plan_test_hook")
 
 
 def dbscan_batch(plan: int, instances, per_inst=None) -> int:

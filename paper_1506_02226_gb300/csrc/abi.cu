@@ -178,7 +178,10 @@ int plan_run(dbscan_plan *plan, const float *points, int64_t n, int32_t d, float
         }
         if (want_tc && tc_ok) {
             path = DBSCAN_PATH_ALLPAIRS_TC;
-            err = launch_allpairs_tc(plan->w, points, n, d, Tc, min_pts, o.precision == DBSCAN_PREC_BF16_GRAM, st);
+            const bool stall = plan->test_hook == DBSCAN_HOOK_TC_STALL;
+            plan->test_hook = DBSCAN_HOOK_NONE;  // consumed by this run
+            err = launch_allpairs_tc(plan->w, points, n, d, Tc, min_pts, o.precision == DBSCAN_PREC_BF16_GRAM, stall,
+                                     st);
         } else {
             const int dp = dp_for(d);
             if (dp < 0) return DBSCAN_ERR_UNSUPPORTED;
@@ -414,6 +417,12 @@ int dbscan_plan_counters(dbscan_plan *plan, uint64_t *out, int32_t n) {
         cudaStreamSynchronize(plan->stream) != cudaSuccess)
         return DBSCAN_ERR_CUDA;
     for (int i = 0; i < k; ++i) out[i] = plan->h_ctr[i];
+    return DBSCAN_OK;
+}
+
+int dbscan_plan_test_hook(dbscan_plan *plan, int32_t hook) {
+    if (!plan || hook < DBSCAN_HOOK_NONE || hook > DBSCAN_HOOK_TC_STALL) return DBSCAN_ERR_ARG;
+    plan->test_hook = hook;
     return DBSCAN_OK;
 }
 

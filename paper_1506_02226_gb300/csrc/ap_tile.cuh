@@ -47,6 +47,7 @@ __device__ __forceinline__ void ap_tile_body(const ApArgs &a, int rt, int ct_beg
     __shared__ __align__(16) float Bs[DP][BN];
     __shared__ float An[BM], Bn[BN];
     __shared__ uint8_t Ac[BM], Bc[BN];
+    __shared__ uint8_t Aiso[BM];  // border: the row has no neighbour but itself
 
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int row0 = rt * BM;
@@ -60,6 +61,10 @@ __device__ __forceinline__ void ap_tile_body(const ApArgs &a, int rt, int ct_beg
     }
     if (PASS != PASS_COUNT)
         for (int r = tid; r < BM; r += NT) Ac[r] = (row0 + r < a.n) ? a.core[row0 + r] : 0;
+    // A non-core point's count is exact (the count pass never stops early on a
+    // tile holding one), so a count of 1 means no neighbour but itself.
+    if (PASS == PASS_BORDER)
+        for (int r = tid; r < BM; r += NT) Aiso[r] = (row0 + r < a.n) && !Ac[r] && a.count[row0 + r] <= 1;
     __syncthreads();
     if (MODE == MODE_GRAM) {
         // Per-row terms hoisted out of the pair loop (Section IV-B): T+1-|p|^2 and 2p.
@@ -78,7 +83,7 @@ __device__ __forceinline__ void ap_tile_body(const ApArgs &a, int rt, int ct_beg
     if (PASS == PASS_UNION || PASS == PASS_BORDER) {
         int mine = 0;
         for (int r = tid; r < BM; r += NT)
-            if (row0 + r < a.n) mine |= (PASS == PASS_UNION) ? (Ac[r] != 0) : (Ac[r] == 0);
+            if (row0 + r < a.n) mine |= (PASS == PASS_UNION) ? (Ac[r] != 0) : (Ac[r] == 0 && !Aiso[r]);
         want_rows = __syncthreads_or(mine);
     } else {
         __syncthreads();
@@ -232,7 +237,7 @@ __device__ __forceinline__ void ap_tile_body(const ApArgs &a, int rt, int ct_beg
 #pragma unroll
                 for (int o = 8; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
                 const int r = ty * 4 + i;
-                done &= (v != INT_MAX) || (row0 + r >= a.n) || Ac[r];
+                done &= (v != INT_MAX) || (row0 + r >= a.n) || Ac[r] || Aiso[r];
             }
             if (__syncthreads_and(done)) break;
         }

@@ -84,7 +84,9 @@ struct TcArgs {
     int T;                // threshold (< 2^24)
     int bf16;
     int pass;
-    int upper;            // union: only pairs i < j of one list
+    int upper;                   // union: only pairs i < j of one list
+    unsigned long long wait_ns;  // budget of every barrier wait
+    int stall;                   // test hook: the MMA issuer issues nothing
     const int16_t *v16;   // centred units by point index, row stride K (exact recheck)
     int *count;
     int *parent;
@@ -144,14 +146,15 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t pari
 // Bounded wait: about two seconds, or until another role has given up.
 // Waiting threads sleep inside try_wait, so they take no issue slots from the
 // epilogue warps sharing their SM sub-partition.
-__device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+__device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                       unsigned long long budget_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     while (true) {
         for (int i = 0; i < 8; ++i)
             if (mbar_try_wait_sleep(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (globaltimer() - t0 > 2000000000ull) {
+        if (globaltimer() - t0 > budget_ns) {
             *abort_flag = 1;
             return false;
         }
@@ -360,13 +363,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(TcArgs a) {
                 int rt, c0, c1;
                 item_range(a, w, nR, nC, rt, c0, c1);
                 const int ab = ia & 1;
-                if (!mbar_wait(&S.a_empty[ab], ((ia >> 1) & 1) ^ 1, abort_flag)) break;
+                if (!mbar_wait(&S.a_empty[ab], ((ia >> 1) & 1) ^ 1, abort_flag, a.wait_ns)) break;
                 mbar_arrive_expect_tx(&S.a_full[ab], a_bytes + sizeof(MetaBlock));
                 bulk_g2s(S.A[ab], a.opR + (size_t)rt * TM * K, a_bytes, &S.a_full[ab]);
                 bulk_g2s(&S.metaA[ab], a.metaR + rt, sizeof(MetaBlock), &S.a_full[ab]);
                 for (int ct = c0; ct < c1; ++ct, ++t) {
                     const int s = t % NSTAGE;
-                    if (!TC_WAIT(w_prod, mbar_wait(&S.b_empty[s], ((t / NSTAGE) & 1) ^ 1, abort_flag))) break;
+                    if (!TC_WAIT(w_prod, mbar_wait(&S.b_empty[s], ((t / NSTAGE) & 1) ^ 1, abort_flag, a.wait_ns))) break;
                     mbar_arrive_expect_tx(&S.b_full[s], b_bytes + 2 * sizeof(MetaBlock));
                     bulk_g2s(S.B[s], a.opC + (size_t)ct * TN * K, b_bytes, &S.b_full[s]);
                     bulk_g2s(&S.metaB[s][0], a.metaC + 2 * ct, 2 * sizeof(MetaBlock), &S.b_full[s]);
@@ -378,7 +381,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(TcArgs a) {
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
-        if (lane == 0) {
+        // (test hook a.stall: it issues nothing, so the other roles' bounded
+        // waits expire and the CTA takes the abort path with no MMA in flight)
+        if (lane == 0 && !a.stall) {
             const uint32_t idesc = idesc_f16(BF16);
             int t = 0, ia = 0;
             bool clean = true;
@@ -386,13 +391,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(TcArgs a) {
                 int rt, c0, c1;
                 item_range(a, w, nR, nC, rt, c0, c1);
                 const int ab = ia & 1;
-                if (!mbar_wait(&S.a_full[ab], (ia >> 1) & 1, abort_flag)) break;
+                if (!mbar_wait(&S.a_full[ab], (ia >> 1) & 1, abort_flag, a.wait_ns)) break;
                 const uint32_t a_addr = smem_u32(S.A[ab]);
                 bool ok = true;
                 for (int ct = c0; ct < c1; ++ct, ++t) {
                     const int s = t % NSTAGE, b = t & 1;
-                    if (!TC_WAIT(w_mma_b, mbar_wait(&S.b_full[s], (t / NSTAGE) & 1, abort_flag)) ||
-                        !TC_WAIT(w_mma_t, mbar_wait(&S.t_empty[b], ((t >> 1) & 1) ^ 1, abort_flag))) {
+                    if (!TC_WAIT(w_mma_b, mbar_wait(&S.b_full[s], (t / NSTAGE) & 1, abort_flag, a.wait_ns)) ||
+                        !TC_WAIT(w_mma_t, mbar_wait(&S.t_empty[b], ((t >> 1) & 1) ^ 1, abort_flag, a.wait_ns))) {
                         ok = false;
                         break;
                     }
@@ -418,11 +423,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(TcArgs a) {
             if (clean && !*abort_flag) {
                 for (int s = 0; s < NSTAGE && s < t; ++s) {
                     const int ts = s + ((t - 1 - s) / NSTAGE) * NSTAGE;
-                    mbar_wait(&S.b_empty[s], (ts / NSTAGE) & 1, abort_flag);
+                    mbar_wait(&S.b_empty[s], (ts / NSTAGE) & 1, abort_flag, a.wait_ns);
                 }
                 for (int ab = 0; ab < 2 && ab < ia; ++ab) {
                     const int il = ab + ((ia - 1 - ab) / 2) * 2;
-                    mbar_wait(&S.a_empty[ab], (il >> 1) & 1, abort_flag);
+                    mbar_wait(&S.a_empty[ab], (il >> 1) & 1, abort_flag, a.wait_ns);
                 }
             }
         }
@@ -440,7 +445,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(TcArgs a) {
             int rt, c0, c1;
             item_range(a, w, nR, nC, rt, c0, c1);
             const int ab = ia & 1;
-            if (!__all_sync(0xffffffffu, mbar_wait(&S.a_full[ab], (ia >> 1) & 1, abort_flag))) break;
+            if (!__all_sync(0xffffffffu, mbar_wait(&S.a_full[ab], (ia >> 1) & 1, abort_flag, a.wait_ns))) break;
             const float beta_p = S.metaA[ab].beta[r], rho_p = S.metaA[ab].rho[r];
             const int p = S.metaA[ab].idx[r];
             __syncwarp();
@@ -456,7 +461,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(TcArgs a) {
             for (int ct = c0; ct < c1; ++ct, ++t) {
                 const int s = t % NSTAGE, b = t & 1;
                 // warp-uniform outcome: the accumulator loads below are warp-collective
-                if (!__all_sync(0xffffffffu, TC_WAIT(w_epi, mbar_wait(&S.t_full[b], (t >> 1) & 1, abort_flag)))) {
+                if (!__all_sync(0xffffffffu, TC_WAIT(w_epi, mbar_wait(&S.t_full[b], (t >> 1) & 1, abort_flag, a.wait_ns)))) {
                     ok = false;
                     break;
                 }
@@ -785,7 +790,7 @@ cudaError_t launch_pass(const TcArgs &a, int sms, cudaStream_t st) {
 
 // Host launcher of the whole tensor-core all-pairs pipeline.
 cudaError_t launch_allpairs_tc(const DbWork &w, const float *x, int64_t n64, int32_t d, int64_t Tc, int32_t min_pts,
-                               bool bf16, cudaStream_t st) {
+                               bool bf16, bool stall, cudaStream_t st) {
     const int n = (int)n64;
     const int K = ((d + 15) / 16) * 16;
     const int n_pad = ((n + TN - 1) / TN) * TN;
@@ -815,7 +820,11 @@ cudaError_t launch_allpairs_tc(const DbWork &w, const float *x, int64_t n64, int
     a.status = w.status;
     a.ctr = w.ctr;
     a.col_chunk = 32;
-    // pass 1: all x all -> neighbour counts
+    a.wait_ns = 2000000000ull;  // about two seconds per barrier wait
+    // pass 1: all x all -> neighbour counts (the stall hook: a 50 ms budget the
+    // waits exhaust, since no MMA completes)
+    a.stall = stall ? 1 : 0;
+    if (stall) a.wait_ns = 50000000ull;
     a.opR = a.opC = w.opAll;
     a.metaR = a.metaC = reinterpret_cast<const MetaBlock *>(w.metaAll);
     a.nR_ptr = a.nC_ptr = lens + 2;
@@ -823,6 +832,8 @@ cudaError_t launch_allpairs_tc(const DbWork &w, const float *x, int64_t n64, int
     a.upper = 0;
     if ((e = launch_pass<TC_COUNT>(a, sms, st))) return e;
     w.marks->kernel("tc_count", st);
+    a.stall = 0;
+    a.wait_ns = 2000000000ull;
     // core flags, parent, border init (shared with the SIMT path)
     launch_core_init(w, n, min_pts, st);
     // core / non-core lists
@@ -890,6 +901,7 @@ cudaError_t launch_tc_verify(const DbWork &w, const float *x, int64_t n64, int32
     a.status = w.status;
     a.ctr = w.ctr;
     a.col_chunk = 32;
+    a.wait_ns = 2000000000ull;
     a.opR = a.opC = w.opAll;
     a.metaR = a.metaC = reinterpret_cast<const MetaBlock *>(w.metaAll);
     a.nR_ptr = a.nC_ptr = lens + 2;

@@ -196,7 +196,7 @@ cudaError_t launch_allpairs_simt(const DbWork &w, int64_t n, int32_t d, int32_t 
                                  bool exact_counts, cudaStream_t st);
 cudaError_t launch_core_init(const DbWork &w, int64_t n, int32_t min_pts, cudaStream_t st);
 cudaError_t launch_allpairs_tc(const DbWork &w, const float *x, int64_t n, int32_t d, int64_t Tc, int32_t min_pts,
-                               bool bf16, cudaStream_t st);
+                               bool bf16, bool stall, cudaStream_t st);
 cudaError_t launch_tc_verify(const DbWork &w, const float *x, int64_t n, int32_t d, int64_t Tc, bool bf16,
                              cudaStream_t st);
 cudaError_t launch_labels_allpairs(const DbWork &w, int64_t n, int32_t *labels, int32_t *counts_out,

@@ -20,6 +20,7 @@ struct dbscan_plan {
     size_t extra_bytes = 0;
     BatchState *batch = nullptr;  // dbscan_batch state (allocated on first use)
     PhaseMarks marks;             // per-kernel events (opts.profile)
+    int test_hook = 0;            // dbscan_plan_test_hook, consumed by the next run it applies to
 };
 
 int plan_run(dbscan_plan *plan, const float *points, int64_t n, int32_t d, float eps, int32_t min_pts,
