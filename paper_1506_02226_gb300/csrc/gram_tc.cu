@@ -32,14 +32,16 @@
 // contiguous block, fetched by a single cp.async.bulk (TMA) copy.  Per-point
 // metadata {beta, rho, index} rides along in the same copy group.
 //
-// CTA roles (320 threads, one CTA per SM, persistent over work items):
+// CTA roles (320 threads, 576 for the FP16 count; one CTA per SM, persistent
+// over work items):
 //   warp 0      producer: bulk copies of A tiles (2 buffers) and B tiles
 //               (4-stage ring), completion via mbarrier transaction counts
 //   warp 1      TMEM owner (alloc/dealloc of 512 columns) and MMA issuer:
 //               K/16 tcgen05.mma (M=128, N=256, K=16) per tile into one of two
 //               256-column accumulators; tcgen05.commit signals the epilogue
-//   warps 2..9  epilogue: tcgen05.ld of the accumulator (one TMEM lane = one
-//               row; two warps per lane quadrant split the 256 columns), the
+//   warps 2..   epilogue: tcgen05.ld of the accumulator (one TMEM lane = one
+//               row; two warps per lane quadrant split the 256 columns, four
+//               for the FP16 count), the
 //               exact decision above, and the pass's consumer: neighbour count,
 //               union of core-core neighbours, or smallest core neighbour.
 // Every wait is bounded (about two seconds of %globaltimer); on expiry the CTA
@@ -56,11 +58,23 @@
 
 namespace {
 
-constexpr int TM = 128, TN = 256, NSTAGE = 4, EPI_WARPS = 8, NTHREADS = 32 * (2 + EPI_WARPS);
+constexpr int TM = 128, TN = 256, NSTAGE = 4;
 constexpr int FP16_BAND = 0;  // FP16 Gram products are exact (see above): no band
 constexpr float BF16_E = 0.0078125f + 0.0000152587890625f;  // 2^-7 + 2^-16
 
 enum { TC_COUNT = 0, TC_UNION = 1, TC_BORDER = 2, TC_VERIFY = 3 };
+
+// Epilogue warps per CTA: two per TMEM lane quadrant (128 columns each), or
+// four (64 columns each) for the FP16 count, whose light per-pair work needs
+// more warps in flight to hide its latencies.
+template <int PASS, bool BF16>
+constexpr int epi_warps() {
+    return (PASS == TC_COUNT && !BF16) ? 16 : 8;
+}
+template <int PASS, bool BF16>
+constexpr int tc_threads() {
+    return 32 * (2 + epi_warps<PASS, BF16>());
+}
 
 // Per-point metadata, in list order, stored as one 2 KB block per 128 points:
 // beta[128] (|v|^2), rho[128] (BF16 band factor), idx[128] (point index, -1
@@ -159,6 +173,28 @@ __device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile 
             return false;
         }
     }
+}
+
+// Packed FP32 pairs (sm_100 and later): two lanes of arithmetic per
+// instruction, each rounded exactly as its scalar counterpart.
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
 }
 
 // Optional pipeline diagnostics (compile with -DDB_TC_WAIT_STATS): cycles each
@@ -314,7 +350,9 @@ __device__ __noinline__ int unite_root(int *parent, int p, int q, unsigned *stat
 
 
 template <int PASS, bool BF16>
-__global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(TcArgs a) {
+__global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(TcArgs a) {
+    constexpr int EPI_WARPS = epi_warps<PASS, BF16>();
+    constexpr int NG = 16 / EPI_WARPS;  // 64-column groups per epilogue warp and tile
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // Align by pointer arithmetic on the shared array (not through an integer),
     // so the compiler keeps shared-space loads, stores and atomics.
@@ -433,10 +471,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(TcArgs a) {
         }
     } else {
         // ---------------- epilogue ----------------
-        const int ew = warp - 2;         // 0..7
-        const int quad = warp & 3;       // TMEM lane quadrant this warp may access
-        const int half = ew >> 2;        // column half of the 256-column tile
-        const int r = quad * 32 + lane;  // row within the tile
+        const int ew = warp - 2;                  // 0..EPI_WARPS-1
+        const int quad = warp & 3;                // TMEM lane quadrant this warp may access
+        const int colbase = (ew >> 2) * 64 * NG;  // first column of this warp in the 256-column tile
+        const int half = colbase >> 7;            // 128-column metadata block holding it
+        const int moff = colbase & 127;           // its offset in that block
+        const int r = quad * 32 + lane;           // row within the tile
         const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
         int t = 0, ia = 0;
         unsigned long long band_cnt = 0, bad_cnt = 0;
@@ -470,8 +510,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(TcArgs a) {
                 int *colroot = S.colroot[b][half];
                 bool hints = false;  // union: colroot filled for this tile
 #pragma unroll 1
-                for (int hc = 0; hc < 2; ++hc) {
-                    const int cb = hc * 64;  // column within this warp's 128-column half
+                for (int hc = 0; hc < NG; ++hc) {
+                    const int cb = moff + hc * 64;  // column within the 128-column block
                     uint32_t g[64];
                     const uint32_t taddr = tmem + lane_base + (uint32_t)(b * TN + half * 128 + cb);
                     tmem_ld32_nowait(taddr, g);
@@ -501,48 +541,87 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pass_kernel(TcArgs a) {
                     }
                     if (PASS == TC_COUNT && !BF16) {
                         // FP16 count: G is exact, so sat(2G - |v_q|^2 + 1 - alpha) is
-                        // exactly 1 for a neighbour (T - D + 1 >= 1) and 0 otherwise;
-                        // three branch-free FP32 ops per pair.
+                        // exactly 1 for a neighbour (T - D + 1 >= 1) and 0 otherwise.
+                        // Two pairs per packed FFMA (w' = |v_q|^2 - 2G, the exact
+                        // negation of fma(2, G, -|v_q|^2): round-to-nearest is
+                        // symmetric), one saturating subtract per pair (c1 - w' =
+                        // c1 + w, the same rounding as before) and one packed add per
+                        // two pairs: two FP32-pipe instructions per pair.
                         const float c1 = 1.f - alpha;
-                        float acc0 = 0.f, acc1 = 0.f;
+                        const unsigned long long m2 = f2_pack(-2.f, -2.f);
+                        unsigned long long acc01 = 0ull, acc23 = 0ull;  // +0.0f in both halves
 #pragma unroll
                         for (int j4 = 0; j4 < 16; ++j4) {
                             const float4 b4 = *reinterpret_cast<const float4 *>(&mc.beta[cb + 4 * j4]);
-                            acc0 += __saturatef(fmaf(2.f, __uint_as_float(g[4 * j4 + 0]), -b4.x) + c1);
-                            acc1 += __saturatef(fmaf(2.f, __uint_as_float(g[4 * j4 + 1]), -b4.y) + c1);
-                            acc0 += __saturatef(fmaf(2.f, __uint_as_float(g[4 * j4 + 2]), -b4.z) + c1);
-                            acc1 += __saturatef(fmaf(2.f, __uint_as_float(g[4 * j4 + 3]), -b4.w) + c1);
+                            const unsigned long long w01 =
+                                f2_fma(f2_pack(__uint_as_float(g[4 * j4 + 0]), __uint_as_float(g[4 * j4 + 1])), m2,
+                                       f2_pack(b4.x, b4.y));
+                            const unsigned long long w23 =
+                                f2_fma(f2_pack(__uint_as_float(g[4 * j4 + 2]), __uint_as_float(g[4 * j4 + 3])), m2,
+                                       f2_pack(b4.z, b4.w));
+                            float w0, w1, w2, w3;
+                            f2_unpack(w01, w0, w1);
+                            f2_unpack(w23, w2, w3);
+                            acc01 = f2_add(acc01, f2_pack(__saturatef(c1 - w0), __saturatef(c1 - w1)));
+                            acc23 = f2_add(acc23, f2_pack(__saturatef(c1 - w2), __saturatef(c1 - w3)));
                         }
-                        if (row_ok) cnt += (int)(acc0 + acc1);
+                        float s0, s1, s2, s3;
+                        f2_unpack(acc01, s0, s1);
+                        f2_unpack(acc23, s2, s3);
+                        if (row_ok) cnt += (int)((s0 + s1) + (s2 + s3));
                         continue;
                     }
                     // Union / border / BF16: per pair one FFMA (two for BF16); the
                     // maxima of the eight strided column groups (j mod 8) come from
                     // the first three levels of an FMNMX tree.  Only groups whose
                     // maximum can reach the threshold are rescanned.
-                    float wv[64];
-#pragma unroll
-                    for (int j4 = 0; j4 < 16; ++j4) {
-                        const float4 b4 = *reinterpret_cast<const float4 *>(&mc.beta[cb + 4 * j4]);
-                        wv[4 * j4 + 0] = fmaf(2.f, __uint_as_float(g[4 * j4 + 0]), -b4.x);
-                        wv[4 * j4 + 1] = fmaf(2.f, __uint_as_float(g[4 * j4 + 1]), -b4.y);
-                        wv[4 * j4 + 2] = fmaf(2.f, __uint_as_float(g[4 * j4 + 2]), -b4.z);
-                        wv[4 * j4 + 3] = fmaf(2.f, __uint_as_float(g[4 * j4 + 3]), -b4.w);
-                        if (BF16) {
-                            const float4 r4 = *reinterpret_cast<const float4 *>(&mc.rho[cb + 4 * j4]);
-                            wv[4 * j4 + 0] = fmaf(rho_p, r4.x, wv[4 * j4 + 0]);
-                            wv[4 * j4 + 1] = fmaf(rho_p, r4.y, wv[4 * j4 + 1]);
-                            wv[4 * j4 + 2] = fmaf(rho_p, r4.z, wv[4 * j4 + 2]);
-                            wv[4 * j4 + 3] = fmaf(rho_p, r4.w, wv[4 * j4 + 3]);
-                        }
-                    }
-#pragma unroll
-                    for (int w2 = 32; w2 >= 8; w2 >>= 1)
-#pragma unroll
-                        for (int j = 0; j < w2; ++j) wv[j] = fmaxf(wv[j], wv[j + w2]);
+                    // Candidate score per pair: 2G - |v_q|^2 (+ rho_p rho_q for BF16);
+                    // a group needs its rare path when the maximum reaches alpha.
+                    // FP16 computes the exact negation |v_q|^2 - 2G two pairs per packed
+                    // FFMA (round-to-nearest is symmetric) and takes minus its minimum;
+                    // BF16 keeps scalar FFMAs, whose registers fit beside the
+                    // accumulator copy its exact recheck needs.
                     const float thr = BF16 ? alpha : alpha - (float)FP16_BAND;
-                    const float mx = fmaxf(fmaxf(fmaxf(wv[0], wv[1]), fmaxf(wv[2], wv[3])),
-                                           fmaxf(fmaxf(wv[4], wv[5]), fmaxf(wv[6], wv[7])));
+                    float mx;
+                    if (!BF16) {
+                        float nv[64];
+                        const unsigned long long m2 = f2_pack(-2.f, -2.f);
+#pragma unroll
+                        for (int j4 = 0; j4 < 16; ++j4) {
+                            const float4 b4 = *reinterpret_cast<const float4 *>(&mc.beta[cb + 4 * j4]);
+                            const unsigned long long w01 =
+                                f2_fma(f2_pack(__uint_as_float(g[4 * j4 + 0]), __uint_as_float(g[4 * j4 + 1])), m2,
+                                       f2_pack(b4.x, b4.y));
+                            const unsigned long long w23 =
+                                f2_fma(f2_pack(__uint_as_float(g[4 * j4 + 2]), __uint_as_float(g[4 * j4 + 3])), m2,
+                                       f2_pack(b4.z, b4.w));
+                            f2_unpack(w01, nv[4 * j4 + 0], nv[4 * j4 + 1]);
+                            f2_unpack(w23, nv[4 * j4 + 2], nv[4 * j4 + 3]);
+                        }
+#pragma unroll
+                        for (int w2 = 32; w2 >= 8; w2 >>= 1)
+#pragma unroll
+                            for (int j = 0; j < w2; ++j) nv[j] = fminf(nv[j], nv[j + w2]);
+                        mx = -fminf(fminf(fminf(nv[0], nv[1]), fminf(nv[2], nv[3])),
+                                    fminf(fminf(nv[4], nv[5]), fminf(nv[6], nv[7])));
+                    } else {
+                        float wv[64];
+#pragma unroll
+                        for (int j4 = 0; j4 < 16; ++j4) {
+                            const float4 b4 = *reinterpret_cast<const float4 *>(&mc.beta[cb + 4 * j4]);
+                            const float4 r4 = *reinterpret_cast<const float4 *>(&mc.rho[cb + 4 * j4]);
+                            wv[4 * j4 + 0] = fmaf(rho_p, r4.x, fmaf(2.f, __uint_as_float(g[4 * j4 + 0]), -b4.x));
+                            wv[4 * j4 + 1] = fmaf(rho_p, r4.y, fmaf(2.f, __uint_as_float(g[4 * j4 + 1]), -b4.y));
+                            wv[4 * j4 + 2] = fmaf(rho_p, r4.z, fmaf(2.f, __uint_as_float(g[4 * j4 + 2]), -b4.z));
+                            wv[4 * j4 + 3] = fmaf(rho_p, r4.w, fmaf(2.f, __uint_as_float(g[4 * j4 + 3]), -b4.w));
+                        }
+#pragma unroll
+                        for (int w2 = 32; w2 >= 8; w2 >>= 1)
+#pragma unroll
+                            for (int j = 0; j < w2; ++j) wv[j] = fmaxf(wv[j], wv[j + w2]);
+                        mx = fmaxf(fmaxf(fmaxf(wv[0], wv[1]), fmaxf(wv[2], wv[3])),
+                                   fmaxf(fmaxf(wv[4], wv[5]), fmaxf(wv[6], wv[7])));
+                    }
                     // Border: the columns are core points in ascending index order,
                     // so a group whose first index is not below the best so far
                     // cannot improve it.
@@ -777,7 +856,7 @@ cudaError_t launch_pass_t(const TcArgs &a, int sms, cudaStream_t st) {
         if (e) return e;
         attr = true;
     }
-    tc_pass_kernel<PASS, BF16><<<sms, NTHREADS, tc_smem_bytes(), st>>>(a);
+    tc_pass_kernel<PASS, BF16><<<sms, tc_threads<PASS, BF16>(), tc_smem_bytes(), st>>>(a);
     return cudaGetLastError();
 }
 
