@@ -32,16 +32,16 @@
 // contiguous block, fetched by a single cp.async.bulk (TMA) copy.  Per-point
 // metadata {beta, rho, index} rides along in the same copy group.
 //
-// CTA roles (320 threads, 576 for the FP16 count; one CTA per SM, persistent
-// over work items):
+// CTA roles (576 threads for FP16, 320 for BF16 and verification; one CTA
+// per SM, persistent over work items):
 //   warp 0      producer: bulk copies of A tiles (2 buffers) and B tiles
 //               (4-stage ring), completion via mbarrier transaction counts
 //   warp 1      TMEM owner (alloc/dealloc of 512 columns) and MMA issuer:
 //               K/16 tcgen05.mma (M=128, N=256, K=16) per tile into one of two
 //               256-column accumulators; tcgen05.commit signals the epilogue
 //   warps 2..   epilogue: tcgen05.ld of the accumulator (one TMEM lane = one
-//               row; two warps per lane quadrant split the 256 columns, four
-//               for the FP16 count), the
+//               row; four warps per lane quadrant split the 256 columns for
+//               FP16, two for BF16), the
 //               exact decision above, and the pass's consumer: neighbour count,
 //               union of core-core neighbours, or smallest core neighbour.
 // Every wait is bounded (about two seconds of %globaltimer); on expiry the CTA
@@ -64,12 +64,19 @@ constexpr float BF16_E = 0.0078125f + 0.0000152587890625f;  // 2^-7 + 2^-16
 
 enum { TC_COUNT = 0, TC_UNION = 1, TC_BORDER = 2, TC_VERIFY = 3 };
 
-// Epilogue warps per CTA: two per TMEM lane quadrant (128 columns each), or
-// four (64 columns each) for the FP16 count, whose light per-pair work needs
-// more warps in flight to hide its latencies.
+// Epilogue warps per CTA: four per TMEM lane quadrant (64 columns each) for
+// the FP16 passes, whose light per-pair work needs many warps in flight to hide
+// its latencies; two (128 columns each) for BF16 and the verification pass,
+// whose register footprint allows no more.  Columns are taken in groups of
+// 64, or 32 for the FP16 merge and border passes (their candidate scores and
+// the accumulator copy then fit the 16-warp register budget).
 template <int PASS, bool BF16>
 constexpr int epi_warps() {
-    return (PASS == TC_COUNT && !BF16) ? 16 : 8;
+    return (!BF16 && PASS != TC_VERIFY) ? 16 : 8;
+}
+template <int PASS, bool BF16>
+constexpr int group_cols() {
+    return (!BF16 && (PASS == TC_UNION || PASS == TC_BORDER)) ? 32 : 64;
 }
 template <int PASS, bool BF16>
 constexpr int tc_threads() {
@@ -352,7 +359,8 @@ __device__ __noinline__ int unite_root(int *parent, int p, int q, unsigned *stat
 template <int PASS, bool BF16>
 __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(TcArgs a) {
     constexpr int EPI_WARPS = epi_warps<PASS, BF16>();
-    constexpr int NG = 16 / EPI_WARPS;  // 64-column groups per epilogue warp and tile
+    constexpr int GW = group_cols<PASS, BF16>();    // columns per group
+    constexpr int NG = (1024 / EPI_WARPS) / GW;     // groups per epilogue warp and tile
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // Align by pointer arithmetic on the shared array (not through an integer),
     // so the compiler keeps shared-space loads, stores and atomics.
@@ -473,7 +481,7 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
         // ---------------- epilogue ----------------
         const int ew = warp - 2;                  // 0..EPI_WARPS-1
         const int quad = warp & 3;                // TMEM lane quadrant this warp may access
-        const int colbase = (ew >> 2) * 64 * NG;  // first column of this warp in the 256-column tile
+        const int colbase = (ew >> 2) * (1024 / EPI_WARPS);  // first column of this warp in the tile
         const int half = colbase >> 7;            // 128-column metadata block holding it
         const int moff = colbase & 127;           // its offset in that block
         const int r = quad * 32 + lane;           // row within the tile
@@ -509,21 +517,31 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
                 const MetaBlock &mc = S.metaB[s][half];
                 int *colroot = S.colroot[b][half];
                 bool hints = false;  // union: colroot filled for this tile
+                // union: the parents of this tile's 128 column points, loaded now so
+                // that their latency hides behind the accumulator loads and scores
+                int pr[4] = {-1, -1, -1, -1};
+                if (PASS == TC_UNION) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int q = mc.idx[lane + 32 * k];
+                        if (q >= 0) pr[k] = db::ld_relaxed(a.parent + q);
+                    }
+                }
 #pragma unroll 1
                 for (int hc = 0; hc < NG; ++hc) {
-                    const int cb = moff + hc * 64;  // column within the 128-column block
-                    uint32_t g[64];
+                    const int cb = moff + hc * GW;  // column within the 128-column block
+                    uint32_t g[GW];
                     const uint32_t taddr = tmem + lane_base + (uint32_t)(b * TN + half * 128 + cb);
                     tmem_ld32_nowait(taddr, g);
-                    tmem_ld32_nowait(taddr + 32, g + 32);
+                    if constexpr (GW == 64) tmem_ld32_nowait(taddr + 32, g + 32);
                     tmem_wait_ld();
                     if (PASS == TC_VERIFY) {
                         if (!row_ok) continue;
 #pragma unroll 1
-                        for (int j = 0; j < 64; ++j) {
+                        for (int j = 0; j < GW; ++j) {
                             const int q = mc.idx[cb + j];
                             if (q < 0) continue;
-                            const float gv = __uint_as_float(g[j & 63]);
+                            const float gv = __uint_as_float(g[j & (GW - 1)]);
                             const float wv = fmaf(2.f, gv, -mc.beta[cb + j]);
                             const int D = exact_sqdist(a.v16, K, p, q);
                             // 2G exactly, from integers: |v_p|^2 + |v_q|^2 - D (the betas are exact)
@@ -584,10 +602,10 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
                     const float thr = BF16 ? alpha : alpha - (float)FP16_BAND;
                     float mx;
                     if (!BF16) {
-                        float nv[64];
+                        float nv[GW];
                         const unsigned long long m2 = f2_pack(-2.f, -2.f);
 #pragma unroll
-                        for (int j4 = 0; j4 < 16; ++j4) {
+                        for (int j4 = 0; j4 < GW / 4; ++j4) {
                             const float4 b4 = *reinterpret_cast<const float4 *>(&mc.beta[cb + 4 * j4]);
                             const unsigned long long w01 =
                                 f2_fma(f2_pack(__uint_as_float(g[4 * j4 + 0]), __uint_as_float(g[4 * j4 + 1])), m2,
@@ -599,15 +617,15 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
                             f2_unpack(w23, nv[4 * j4 + 2], nv[4 * j4 + 3]);
                         }
 #pragma unroll
-                        for (int w2 = 32; w2 >= 8; w2 >>= 1)
+                        for (int w2 = GW / 2; w2 >= 8; w2 >>= 1)
 #pragma unroll
                             for (int j = 0; j < w2; ++j) nv[j] = fminf(nv[j], nv[j + w2]);
                         mx = -fminf(fminf(fminf(nv[0], nv[1]), fminf(nv[2], nv[3])),
                                     fminf(fminf(nv[4], nv[5]), fminf(nv[6], nv[7])));
                     } else {
-                        float wv[64];
+                        float wv[GW];
 #pragma unroll
-                        for (int j4 = 0; j4 < 16; ++j4) {
+                        for (int j4 = 0; j4 < GW / 4; ++j4) {
                             const float4 b4 = *reinterpret_cast<const float4 *>(&mc.beta[cb + 4 * j4]);
                             const float4 r4 = *reinterpret_cast<const float4 *>(&mc.rho[cb + 4 * j4]);
                             wv[4 * j4 + 0] = fmaf(rho_p, r4.x, fmaf(2.f, __uint_as_float(g[4 * j4 + 0]), -b4.x));
@@ -616,7 +634,7 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
                             wv[4 * j4 + 3] = fmaf(rho_p, r4.w, fmaf(2.f, __uint_as_float(g[4 * j4 + 3]), -b4.w));
                         }
 #pragma unroll
-                        for (int w2 = 32; w2 >= 8; w2 >>= 1)
+                        for (int w2 = GW / 2; w2 >= 8; w2 >>= 1)
 #pragma unroll
                             for (int j = 0; j < w2; ++j) wv[j] = fmaxf(wv[j], wv[j + w2]);
                         mx = fmaxf(fmaxf(fmaxf(wv[0], wv[1]), fmaxf(wv[2], wv[3])),
@@ -628,21 +646,15 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
                     const bool need = row_ok && mx >= thr && (PASS != TC_BORDER || mc.idx[cb] < bmin);
                     if (!__any_sync(0xffffffffu, need)) continue;
                     if (PASS == TC_UNION && !hints) {
-                        // parents of this tile's 128 column points, four loads per lane
-                        // (the four warps of the half all write them: any value is a
-                        // member of the column point's set)
-                        int pr[4];
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            const int q = mc.idx[lane + 32 * k];
-                            pr[k] = q >= 0 ? db::ld_relaxed(a.parent + q) : -1;
-                        }
+                        // the parents loaded at the tile's start (the four warps of the
+                        // half all write them: any value is a member of the column
+                        // point's set)
 #pragma unroll
                         for (int k = 0; k < 4; ++k) colroot[lane + 32 * k] = pr[k];
                         __syncwarp();
                         hints = true;
                     }
-                    // Rare path: the lanes that need it build the 64-bit mask of
+                    // Rare path: the lanes that need it build the mask of
                     // possible neighbours (for FP16 exactly the neighbours; padding
                     // columns never pass, their beta is 1e30).  The merge pass also
                     // drops the columns whose set hint equals the row's: those pairs
@@ -651,7 +663,7 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
                     if (need) {
                         const int col_lim = a.upper ? (i_row - (ct * TN + half * 128)) : -1;  // cols <= this: j <= i
 #pragma unroll
-                        for (int j = 0; j < 64; ++j) {
+                        for (int j = 0; j < GW; ++j) {
                             const float w1 = fmaf(2.f, __uint_as_float(g[j]), -mc.beta[cb + j]);
                             bool c = BF16 ? (fmaf(rho_p, mc.rho[cb + j], w1) >= alpha) : (w1 >= alpha);
                             if (PASS == TC_UNION) c = c && colroot[cb + j] != rootp;
@@ -667,7 +679,7 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
                             // recompute 2G - |v_q|^2 for column j from the accumulator copy in g
                             float gj = 0.f;
 #pragma unroll
-                            for (int k = 0; k < 64; ++k)
+                            for (int k = 0; k < GW; ++k)
                                 if (k == j) gj = __uint_as_float(g[k]);
                             const float wj = fmaf(2.f, gj, -mc.beta[cb + j]);
                             const int res = decide_candidate<BF16>(wj, alpha, rho_p, mc.rho[cb + j], a.v16, K, p, q, a.T);
