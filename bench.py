@@ -304,9 +304,19 @@ def cpu_baseline(inst, wl_name, desc):
     oracle.dbscan(sub.points, sub.eps, sub.min_pts, nthreads=cores)
     dt = time.perf_counter() - t0
     units = work_units(sub.points, sub.eps, sub.d)
+    # the same oracle on one thread, on a sample a quarter the size (brute force
+    # and the candidate count both scale as n^2, so the rate compares)
+    m1 = max(m // 4, min(m, 1000))
+    sub1 = inputs.subsample(inst, m1, seed=12345)
+    t1 = time.perf_counter()
+    oracle.dbscan(sub1.points, sub1.eps, sub1.min_pts, nthreads=1)
+    dt1 = time.perf_counter() - t1
+    units1 = work_units(sub1.points, sub1.eps, sub1.d)
     return {"value": units / dt / 1e9, "unit": "G pair-tests/s", "cores": cores, "kind": "oracle",
             "sample": f"full oracle run on a {m}-point uniform subsample of the {desc} workload "
-                      f"({units} pair tests, {dt:.2f} s)"}
+                      f"({units} pair tests, {dt:.2f} s)",
+            "single_thread": {"value": units1 / dt1 / 1e9, "cores": 1,
+                              "sample": f"{m1}-point subsample ({units1} pair tests, {dt1:.2f} s)"}}
 
 
 def run_batch(args):
@@ -649,6 +659,12 @@ def run_ours(args, wl_name):
         roof = {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": args.traffic, "peak_src": peaks["src"], "algorithmic_flops": flops,
                 "avg_ms": avg[dom]}
+        # the epilogue beside the MMA: about 3 FP32 operations per pair (the exact
+        # decision and the count), against the FP32 pipe (SMs x 128 lanes x clock)
+        fp32_peak, _ = fp32_peak_tops()
+        alu = 3.0 * pairs / (avg[dom] * 1e-3) / 1e12
+        roof["epilogue_fp32"] = {"ops_per_pair": 3, "achieved": alu, "peak": fp32_peak, "unit": "T ops/s",
+                                 "frac": alu / fp32_peak}
     elif bound == "hbm" and work:
         ach = work / (avg[dom] * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -667,6 +683,11 @@ def run_ours(args, wl_name):
                    "path": {1: "eps-grid", 2: "all-pairs SIMT", 3: "all-pairs tensor-core"}.get(st0["path"]),
                    "l2": "flushed by a 256 MiB write before every timed step", "parallelism": f"replicas x{world}"},
         "pair_tests_per_step": units,
+        # all-pairs paths: pairs the three passes evaluate (n^2 counted, cores^2/2
+        # merged, non-cores x cores bordered) over the n(n-1)/2 minimum
+        "evaluated_vs_min": (None if st0["path"] == B.DBSCAN_PATH_GRID else
+                             (n * n + st0["n_core"] ** 2 / 2 + (n - st0["n_core"]) * st0["n_core"])
+                             / max(n * (n - 1) / 2, 1)),
         "band_pairs_per_step": st0["band_pairs"],
         "points_per_s": world * n / (ms_per_step * 1e-3),
         "clusters": st0["n_clusters"], "core": st0["n_core"], "noise": st0["n_noise"],
