@@ -66,7 +66,7 @@ extern "C" {
 #define DBSCAN_PREC_AUTO 0       /* tensor-core FP16 Gram for d >= 16 all-pairs, SIMT otherwise */
 #define DBSCAN_PREC_EXACT_SIMT 1 /* FP32/INT32 CUDA-core pair test, exact by construction */
 #define DBSCAN_PREC_FP16_GRAM 2  /* tcgen05 FP16 Gram product + exact recheck of the rounding band */
-#define DBSCAN_PREC_BF16_GRAM 3  /* tcgen05 BF16 Gram product + exact recheck of the rounding band */
+#define DBSCAN_PREC_BF16_GRAM 3  /* tcgen05 BF16 Gram product (two-term split) + exact recheck of the band */
 
 /* Candidate generation. */
 #define DBSCAN_GRID_AUTO 0 /* eps-grid for d <= 3, all pairs otherwise */
@@ -174,7 +174,7 @@ typedef struct dbscan_tc_report {
     int64_t band_pairs;         /* pairs inside the band, which the fast path rechecks */
     int64_t wrong_outside_band; /* pairs outside the band decided differently from exact: must be 0 */
     int64_t max_abs_error_2g;   /* largest |2G_tensor - 2G_exact| seen, in squared grid units */
-    int64_t band_halfwidth_2g;  /* FP16 band half-width in the same units (0: exact by proof; -1: per-pair, BF16) */
+    int64_t band_halfwidth_2g;  /* band half-width in the same units (FP16: 0, exact by proof; BF16: 16 K, K = d padded to 16) */
     int64_t threshold;          /* T */
 } dbscan_tc_report;
 int dbscan_tc_verify(dbscan_plan *plan, const float *points, int64_t n, int32_t d, float eps, int32_t bf16,

@@ -88,9 +88,9 @@ size_t layout(DbWork &w, const dbscan_opts &o, char *base) {
         w.tc_cap_pad = np;
         w.v16 = c.take<int16_t>((size_t)n * 64);
         w.inorm = c.take<int32_t>(n);
-        w.opAll = c.take<uint16_t>((size_t)np * 64);
-        w.opCore = c.take<uint16_t>((size_t)np * 64);
-        w.opNon = c.take<uint16_t>((size_t)np * 64);
+        w.opAll = c.take<uint16_t>((size_t)np * 128);
+        w.opCore = c.take<uint16_t>((size_t)np * 128);
+        w.opNon = c.take<uint16_t>((size_t)np * 128);
         w.metaAll = c.take<char>((size_t)np * 16);
         w.metaCore = c.take<char>((size_t)np * 16);
         w.metaNon = c.take<char>((size_t)np * 16);
@@ -403,7 +403,7 @@ int dbscan_tc_verify(dbscan_plan *plan, const float *points, int64_t n, int32_t 
     out->band_pairs = (int64_t)plan->h_ctr[6];
     out->wrong_outside_band = (int64_t)plan->h_ctr[7];
     out->max_abs_error_2g = (int64_t)plan->h_ctr[8];
-    out->band_halfwidth_2g = bf16 ? -1 : 0;
+    out->band_halfwidth_2g = bf16 ? 16 * ((d + 15) / 16 * 16) : 0;  // 16 K for the two BF16 terms
     out->threshold = T;
     return DBSCAN_OK;
 }

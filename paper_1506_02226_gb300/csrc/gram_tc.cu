@@ -17,12 +17,16 @@
 //   same side of alpha.  The stated FP16 band is therefore 0; the diagnostic
 //   pass (TC_VERIFY, dbscan_tc_verify) recomputes every pair exactly on the
 //   device and reports max |2G - 2G_exact| = 0 and no pair decided wrongly.
-//   BF16 (8-bit significand) rounds v, each by at most 2^-8 |v|, so
-//   |G_bf16 - G| <= e |v_p| |v_q| with e = 2^-7 + 2^-16 (Cauchy-Schwarz); the
-//   products of the rounded integers are still integers, so accumulation adds
-//   no error.  A pair is decided directly when |w - alpha| > 2 e |v_p||v_q|
-//   (per-row and per-column factors rho = sqrt(2e) |v| (1 + 2^-10)), and
-//   rechecked exactly otherwise.
+//   BF16 (8-bit significand) cannot hold every v, so each is split into two
+//   BF16 terms, v = hi + lo with hi = bf16(v) and lo = v - hi in {-1, 0, 1}
+//   (both exact), and the MMA sums hi.hi + hi.lo + lo.hi over K, i.e. G minus
+//   sum(lo_p lo_q), |sum| <= K.  Its partial sums stay below
+//   K (512^2 + 2 * 512) < 2^25, so each of the 3K accumulations beyond 2^24
+//   rounds by at most 2: |G_bf16 - G| <= 7K.  With the roundings of w (at most
+//   4 each), a pair is decided directly when |w - alpha| > 16K, and rechecked
+//   exactly otherwise (rho = sqrt(16K) (1 + 2^-10) per row and column, so that
+//   rho_p rho_q covers the band).  The band holds only pairs within 16K
+//   squared units of the threshold.
 //
 // Data layout.  Each operand list (all points, core points, non-core points)
 // is packed once into 128-row tiles in the canonical K-major layout without
@@ -58,9 +62,10 @@
 
 namespace {
 
-constexpr int TM = 128, TN = 256, NSTAGE = 4;
+constexpr int TM = 128, TN = 256;
 constexpr int FP16_BAND = 0;  // FP16 Gram products are exact (see above): no band
-constexpr float BF16_E = 0.0078125f + 0.0000152587890625f;  // 2^-7 + 2^-16
+// BF16 band in units of w = 2G - |v_q|^2 for padded dimension K (see above).
+__host__ __device__ constexpr int bf16_band(int K) { return 16 * K; }
 
 enum { TC_COUNT = 0, TC_UNION = 1, TC_BORDER = 2, TC_VERIFY = 3 };
 
@@ -298,13 +303,18 @@ __device__ __noinline__ int exact_sqdist(const int16_t *__restrict__ v16, int K,
     return s;
 }
 
-struct __align__(16) Smem {
-    uint16_t A[2][TM * 64];          // 2 x 16 KB
-    uint16_t B[NSTAGE][TN * 64];     // 4 x 32 KB
+// Shared memory of one CTA: KC stored operand columns per row (64 for FP16,
+// 128 for the two BF16 terms) and NS stages of B tiles (4 for FP16: 32 KB each;
+// 2 for BF16: 64 KB each).
+template <int KC, int NS>
+struct __align__(16) SmemT {
+    static constexpr int NSTAGE = NS;
+    uint16_t A[2][TM * KC];          // 2 x 16 KB (FP16) or 2 x 32 KB (BF16)
+    uint16_t B[NS][TN * KC];
     MetaBlock metaA[2];              // 2 x 2 KB
-    MetaBlock metaB[NSTAGE][2];      // 4 x 4 KB
+    MetaBlock metaB[NS][2];          // NS x 4 KB
     uint64_t a_full[2], a_empty[2];
-    uint64_t b_full[NSTAGE], b_empty[NSTAGE];
+    uint64_t b_full[NS], b_empty[NS];
     uint64_t t_full[2], t_empty[2];
     uint32_t tmem_base;
     int abort_flag;
@@ -365,6 +375,8 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
     // Align by pointer arithmetic on the shared array (not through an integer),
     // so the compiler keeps shared-space loads, stores and atomics.
     const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
+    using Smem = SmemT<BF16 ? 128 : 64, BF16 ? 2 : 4>;
+    constexpr int NSTAGE = Smem::NSTAGE;
     Smem &S = *reinterpret_cast<Smem *>(smem_raw + pad);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nR = *a.nR_ptr, nC = *a.nC_ptr;
@@ -396,10 +408,12 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = S.tmem_base;
-    const int K = a.K, KG = K / 8;
+    const int K = a.K;
+    const int KS = BF16 ? 2 * K : K;  // stored columns per row: [hi | lo] for BF16
+    const int KG = KS / 8;
     long long w_prod = 0, w_mma_b = 0, w_mma_t = 0, w_epi = 0, t_start = clock64();
     (void)w_prod, (void)w_mma_b, (void)w_mma_t, (void)w_epi, (void)t_start;
-    const uint32_t a_bytes = (uint32_t)(TM * K * 2), b_bytes = (uint32_t)(TN * K * 2);
+    const uint32_t a_bytes = (uint32_t)(TM * KS * 2), b_bytes = (uint32_t)(TN * KS * 2);
 
     if (warp == 0) {
         // ---------------- producer ----------------
@@ -411,13 +425,13 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
                 const int ab = ia & 1;
                 if (!mbar_wait(&S.a_empty[ab], ((ia >> 1) & 1) ^ 1, abort_flag, a.wait_ns)) break;
                 mbar_arrive_expect_tx(&S.a_full[ab], a_bytes + sizeof(MetaBlock));
-                bulk_g2s(S.A[ab], a.opR + (size_t)rt * TM * K, a_bytes, &S.a_full[ab]);
+                bulk_g2s(S.A[ab], a.opR + (size_t)rt * TM * KS, a_bytes, &S.a_full[ab]);
                 bulk_g2s(&S.metaA[ab], a.metaR + rt, sizeof(MetaBlock), &S.a_full[ab]);
                 for (int ct = c0; ct < c1; ++ct, ++t) {
                     const int s = t % NSTAGE;
                     if (!TC_WAIT(w_prod, mbar_wait(&S.b_empty[s], ((t / NSTAGE) & 1) ^ 1, abort_flag, a.wait_ns))) break;
                     mbar_arrive_expect_tx(&S.b_full[s], b_bytes + 2 * sizeof(MetaBlock));
-                    bulk_g2s(S.B[s], a.opC + (size_t)ct * TN * K, b_bytes, &S.b_full[s]);
+                    bulk_g2s(S.B[s], a.opC + (size_t)ct * TN * KS, b_bytes, &S.b_full[s]);
                     bulk_g2s(&S.metaB[s][0], a.metaC + 2 * ct, 2 * sizeof(MetaBlock), &S.b_full[s]);
                 }
             }
@@ -449,10 +463,19 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
                     }
                     tc_fence_after();
                     const uint32_t b_addr = smem_u32(S.B[s]);
-                    for (int kk = 0; kk < K / 16; ++kk) {
+                    // FP16: sum over K of v_p v_q.  BF16: hi.hi + hi.lo + lo.hi, the
+                    // lo columns K/16 chunks after the hi ones (256 B per chunk).
+                    const int kch = K / 16;
+                    for (int kk = 0; kk < kch; ++kk) {
                         const uint64_t ad = smem_desc(a_addr + kk * 256, KG * 128);
                         const uint64_t bd = smem_desc(b_addr + kk * 256, KG * 128);
                         mma_f16(tmem + (uint32_t)(b * TN), ad, bd, idesc, kk > 0 ? 1u : 0u);
+                        if (BF16) {
+                            const uint64_t bl = smem_desc(b_addr + (kch + kk) * 256, KG * 128);
+                            const uint64_t al = smem_desc(a_addr + (kch + kk) * 256, KG * 128);
+                            mma_f16(tmem + (uint32_t)(b * TN), ad, bl, idesc, 1u);
+                            mma_f16(tmem + (uint32_t)(b * TN), al, bd, idesc, 1u);
+                        }
                     }
                     mma_commit(&S.t_full[b]);   // accumulator ready for the epilogue
                     mma_commit(&S.b_empty[s]);  // operands of this stage consumed
@@ -784,13 +807,16 @@ __global__ void tc_prep_kernel(const float *__restrict__ x, int n, int d, int K,
     if (!ok) atomicOr(status, DB_EBIT_NOT_QUANTISED);
 }
 
-__device__ __forceinline__ uint16_t to_half_bits(int v, bool bf16) {
-    if (bf16) {
-        __nv_bfloat16 h = __float2bfloat16_rn((float)v);
-        return *reinterpret_cast<uint16_t *>(&h);
-    }
+__device__ __forceinline__ uint16_t fp16_bits(int v) {
     __half h = __int2half_rn(v);
     return *reinterpret_cast<uint16_t *>(&h);
+}
+__device__ __forceinline__ uint16_t bf16_bits_rn(int v) {
+    __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+    return *reinterpret_cast<uint16_t *>(&h);
+}
+__device__ __forceinline__ int bf16_value(uint16_t bits) {
+    return (int)__uint_as_float((uint32_t)bits << 16);  // an integer for every |v| <= 512
 }
 
 // Packs list entries (list == nullptr: identity) into the tiled operand layout
@@ -800,19 +826,34 @@ __global__ void tc_pack_kernel(const int *__restrict__ list, const int *__restri
                                int bf16, const int16_t *__restrict__ v16, const int *__restrict__ nrm,
                                uint16_t *__restrict__ op, MetaBlock *__restrict__ meta) {
     const int len = *len_ptr;
-    const int KG = K / 8;
+    const int KS = bf16 ? 2 * K : K;  // stored columns: v (FP16), or [hi | lo] (BF16)
+    const int KG = KS / 8, KH = K / 8;
+    const float rho_c = sqrtf((float)bf16_band(K)) * (1.f + 1.f / 1024.f);
     const int64_t total = (int64_t)n_pad * KG;  // one thread per (row, 8-element group)
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(e / KG), kg = (int)(e - (int64_t)i * KG);
-        const int rows_per_tile = TM;
-        const int tile = i / rows_per_tile, r = i - tile * rows_per_tile;
+        const int tile = i / TM, r = i - tile * TM;
         const int rg = r >> 3, ri = r & 7;
         uint16_t h[8];
         const bool valid = i < len;
         const int p = valid ? (list ? list[i] : i) : -1;
+        const bool lo = kg >= KH;  // BF16 only: the remainder columns
+        const int k0 = (lo ? kg - KH : kg) * 8;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) h[k] = valid ? to_half_bits(v16[(size_t)p * K + kg * 8 + k], bf16 != 0) : 0;
-        const size_t off = (size_t)tile * TM * K + ((size_t)(rg * KG + kg) * 64) + ri * 8;
+        for (int k = 0; k < 8; ++k) {
+            if (!valid) {
+                h[k] = 0;
+                continue;
+            }
+            const int v = v16[(size_t)p * K + k0 + k];
+            if (!bf16) {
+                h[k] = fp16_bits(v);
+            } else {
+                const uint16_t hi = bf16_bits_rn(v);
+                h[k] = lo ? bf16_bits_rn(v - bf16_value(hi)) : hi;  // v - hi is -1, 0 or 1: exact
+            }
+        }
+        const size_t off = (size_t)tile * TM * KS + ((size_t)(rg * KG + kg) * 64) + ri * 8;
         uint4 pk;
         pk.x = h[0] | ((uint32_t)h[1] << 16);
         pk.y = h[2] | ((uint32_t)h[3] << 16);
@@ -822,9 +863,8 @@ __global__ void tc_pack_kernel(const int *__restrict__ list, const int *__restri
         if (kg == 0) {
             MetaBlock &m = meta[tile];
             if (valid) {
-                const float nv = (float)nrm[p];
-                m.beta[r] = nv;
-                m.rho[r] = sqrtf(2.f * BF16_E) * sqrtf(nv) * (1.f + 1.f / 1024.f) + 1e-3f;
+                m.beta[r] = (float)nrm[p];
+                m.rho[r] = bf16 ? rho_c : 0.f;
                 m.idx[r] = p;
             } else {
                 m.beta[r] = 1e30f;
@@ -857,18 +897,21 @@ __global__ void core_flags_kernel(int n, const uint8_t *__restrict__ core, int *
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) flags[i] = core[i];
 }
 
-size_t tc_smem_bytes() { return sizeof(Smem) + 1024; }
+template <bool BF16>
+size_t tc_smem_bytes() {
+    return sizeof(SmemT<BF16 ? 128 : 64, BF16 ? 2 : 4>) + 1024;
+}
 
 template <int PASS, bool BF16>
 cudaError_t launch_pass_t(const TcArgs &a, int sms, cudaStream_t st) {
     static bool attr = false;  // one process-wide attribute per instantiation
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(tc_pass_kernel<PASS, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)tc_smem_bytes());
+                                             (int)tc_smem_bytes<BF16>());
         if (e) return e;
         attr = true;
     }
-    tc_pass_kernel<PASS, BF16><<<sms, tc_threads<PASS, BF16>(), tc_smem_bytes(), st>>>(a);
+    tc_pass_kernel<PASS, BF16><<<sms, tc_threads<PASS, BF16>(), tc_smem_bytes<BF16>(), st>>>(a);
     return cudaGetLastError();
 }
 

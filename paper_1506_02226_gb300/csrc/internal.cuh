@@ -172,7 +172,7 @@ struct DbWork {
     int64_t tc_cap_pad;     // rows of each packed operand (cap_n rounded up to 256)
     int16_t *v16;           // centred units v = u - 512 by point index, row stride 64
     int32_t *inorm;         // exact |v|^2 [cap_n]
-    uint16_t *opAll, *opCore, *opNon;  // packed FP16/BF16 operand tiles [tc_cap_pad * 64]
+    uint16_t *opAll, *opCore, *opNon;  // packed FP16 or two-term BF16 operand tiles [tc_cap_pad * 128]
     void *metaAll, *metaCore, *metaNon;  // per-point metadata blocks (16 B per row)
     int32_t *list_a, *list_b;  // core / non-core index lists [cap_n]
     int32_t *tc_lens;       // [0] cores, [1] non-cores, [2] all

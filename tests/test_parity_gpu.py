@@ -296,6 +296,10 @@ def test_tensor_core_band_holds(bf16):
         assert rep["wrong_outside_band"] == 0
         if not bf16:
             assert rep["max_abs_error_2g"] == 0
+        else:  # two-term BF16: the error bound behind the stated band (2 x 7K <= 16K)
+            K = -(-inst.d // 16) * 16
+            assert rep["band_halfwidth_2g"] == 16 * K
+            assert rep["max_abs_error_2g"] <= 14 * K
         want = oracle.counts(inst.points, inst.eps)
         # the verify pass also counts exactly
         with Plan(max_n=inst.n, max_d=inst.d, precision=B.DBSCAN_PREC_BF16_GRAM if bf16 else
