@@ -524,7 +524,6 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
             const int i_row = rt * TM + r;  // list index of this row
             const bool row_ok = i_row < nR && p >= 0;
             const float alpha = beta_p - (float)a.T;  // |v_p|^2 - T, exact
-            const float alo = alpha - (float)FP16_BAND;
             int cnt = 0, bmin = INT_MAX;
             // union: a member of p's set (its parent, then the last root seen)
             int rootp = (PASS == TC_UNION && row_ok) ? db::ld_relaxed(a.parent + p) : -2;
