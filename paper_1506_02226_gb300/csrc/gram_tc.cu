@@ -36,16 +36,16 @@
 // contiguous block, fetched by a single cp.async.bulk (TMA) copy.  Per-point
 // metadata {beta, rho, index} rides along in the same copy group.
 //
-// CTA roles (576 threads for FP16, 320 for BF16 and verification; one CTA
-// per SM, persistent over work items):
+// CTA roles (576 threads, 320 for verification; one CTA per SM, persistent
+// over work items):
 //   warp 0      producer: bulk copies of A tiles (2 buffers) and B tiles
 //               (4-stage ring), completion via mbarrier transaction counts
 //   warp 1      TMEM owner (alloc/dealloc of 512 columns) and MMA issuer:
 //               K/16 tcgen05.mma (M=128, N=256, K=16) per tile into one of two
 //               256-column accumulators; tcgen05.commit signals the epilogue
 //   warps 2..   epilogue: tcgen05.ld of the accumulator (one TMEM lane = one
-//               row; four warps per lane quadrant split the 256 columns for
-//               FP16, two for BF16), the
+//               row; four warps per lane quadrant split the 256 columns, two
+//               for verification), the
 //               exact decision above, and the pass's consumer: neighbour count,
 //               union of core-core neighbours, or smallest core neighbour.
 // Every wait is bounded (about two seconds of %globaltimer); on expiry the CTA
@@ -69,19 +69,18 @@ __host__ __device__ constexpr int bf16_band(int K) { return 16 * K; }
 
 enum { TC_COUNT = 0, TC_UNION = 1, TC_BORDER = 2, TC_VERIFY = 3 };
 
-// Epilogue warps per CTA: four per TMEM lane quadrant (64 columns each) for
-// the FP16 passes, whose light per-pair work needs many warps in flight to hide
-// its latencies; two (128 columns each) for BF16 and the verification pass,
-// whose register footprint allows no more.  Columns are taken in groups of
-// 64, or 32 for the FP16 merge and border passes (their candidate scores and
-// the accumulator copy then fit the 16-warp register budget).
+// Epilogue warps per CTA: four per TMEM lane quadrant (64 columns each), as
+// the light per-pair work needs many warps in flight to hide its latencies;
+// two (128 columns each) for the verification pass.  Columns are taken in
+// groups of 64 for the FP16 count and the verification, else 32 (the candidate
+// scores and the accumulator copy then fit the 16-warp register budget).
 template <int PASS, bool BF16>
 constexpr int epi_warps() {
-    return (!BF16 && PASS != TC_VERIFY) ? 16 : 8;
+    return PASS != TC_VERIFY ? 16 : 8;
 }
 template <int PASS, bool BF16>
 constexpr int group_cols() {
-    return (!BF16 && (PASS == TC_UNION || PASS == TC_BORDER)) ? 32 : 64;
+    return (PASS == TC_VERIFY || (PASS == TC_COUNT && !BF16)) ? 64 : 32;
 }
 template <int PASS, bool BF16>
 constexpr int tc_threads() {
