@@ -320,7 +320,9 @@ def test_tensor_core_high_d_subsample():
 
 @pytest.mark.slow
 def test_full_size_high_d_workload():
-    """n = 200,000, d = 64 on the FP16 tensor-core path, against the full oracle."""
+    """n = 200,000, d = 64 on the FP16 and the two-term BF16 tensor-core paths,
+    against the full oracle."""
+    from paper_1506_02226_gb300.api import Plan
     inst = inputs.high_d()
     want_lab, want_cnt, want_core = oracle.dbscan(inst.points, inst.eps, inst.min_pts)
     lab, cnt, core, st = gpu_detail(inst.points, inst.eps, inst.min_pts)
@@ -330,6 +332,13 @@ def test_full_size_high_d_workload():
     np.testing.assert_array_equal(lab, want_lab)
     lab2, _ = gpu_labels(inst.points, inst.eps, inst.min_pts)
     np.testing.assert_array_equal(lab2, want_lab)
+    lab3, cnt3, core3, st3 = gpu_detail(inst.points, inst.eps, inst.min_pts, precision=B.DBSCAN_PREC_BF16_GRAM)
+    assert st3["path"] == B.DBSCAN_PATH_ALLPAIRS_TC and st3["band_pairs"] > 0
+    np.testing.assert_array_equal(cnt3, want_cnt)
+    np.testing.assert_array_equal(lab3, want_lab)
+    x = torch.from_numpy(inst.points).cuda()
+    with Plan(max_n=inst.n, max_d=inst.d, precision=B.DBSCAN_PREC_BF16_GRAM) as p:  # as bench.py times it
+        np.testing.assert_array_equal(p.run(x, inst.eps, inst.min_pts).cpu().numpy(), want_lab)
 
 
 def test_tensor_core_plan_reused_across_sizes():
