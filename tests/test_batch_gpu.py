@@ -102,3 +102,25 @@ def test_batch_errors():
         assert rc == B.DBSCAN_OK
         for inst, lab in zip(good, labs):
             np.testing.assert_array_equal(lab, oracle.dbscan(inst.points, inst.eps, inst.min_pts)[0])
+
+
+@pytest.mark.slow
+def test_full_batch_workload_sampled_against_oracle():
+    """All 4,096 instances in one dbscan_batch call, as bench.py runs it; every
+    instance against dbscan_run alone, a seeded sample against the oracle."""
+    from paper_1506_02226_gb300.api import Plan
+    insts = inputs.batch(count=4096)
+    with Plan(max_n=16, max_d=16) as bp:
+        rc, labs, st = _run_batch(bp, insts, stats=True)
+        assert rc == B.DBSCAN_OK
+    with Plan(max_n=8192, max_d=16) as single:
+        for k in range(0, 4096, 7):  # every 7th instance against a plain run
+            inst = insts[k]
+            want = single.run(torch.from_numpy(inst.points).cuda(), inst.eps, inst.min_pts).cpu().numpy()
+            np.testing.assert_array_equal(labs[k], want, err_msg=f"instance {k}")
+    rng = np.random.default_rng(99)
+    for k in rng.choice(4096, size=48, replace=False):
+        inst = insts[k]
+        np.testing.assert_array_equal(labs[k], oracle.dbscan(inst.points, inst.eps, inst.min_pts)[0],
+                                      err_msg=f"instance {k}")
+        assert st[k].n_core + st[k].n_border + st[k].n_noise == inst.n

@@ -115,3 +115,23 @@ def test_serve_errors():
         assert B.dbscan_serve_poll(srv, 987654321)[0] == B.DBSCAN_ERR_NOT_FOUND
     finally:
         B.dbscan_serve_destroy(srv)
+
+
+@pytest.mark.slow
+def test_serve_bench_job_pool_alone_and_in_mix():
+    """The 192 seeded jobs bench.py's served workload cycles (n up to 500k, d in
+    {2, 3, 32}): each result in the mix equals the same job run alone, and the
+    smaller jobs equal the oracle."""
+    jobs = []
+    for i in range(192):
+        inst = inputs.serve_job(i)
+        x = torch.from_numpy(inst.points).cuda()
+        jobs.append((inst, x, torch.full((inst.n,), -9, dtype=torch.int32, device="cuda")))
+    want = _alone(jobs)
+    res = _serve(jobs, slots=8, threads=4)
+    for k, ((inst, x, lab), (st, _)) in enumerate(zip(jobs, res)):
+        assert st == B.DBSCAN_OK
+        np.testing.assert_array_equal(lab.cpu().numpy(), want[k], err_msg=f"job {k} n={inst.n} d={inst.d}")
+    small = [j for j in jobs if j[0].n <= 20_000][:24]
+    for inst, x, lab in small:
+        np.testing.assert_array_equal(lab.cpu().numpy(), oracle.dbscan(inst.points, inst.eps, inst.min_pts)[0])
