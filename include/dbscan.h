@@ -65,7 +65,7 @@ extern "C" {
 /* Pair-test arithmetic. */
 #define DBSCAN_PREC_AUTO 0       /* tensor-core FP16 Gram for d >= 16 all-pairs, SIMT otherwise */
 #define DBSCAN_PREC_EXACT_SIMT 1 /* FP32/INT32 CUDA-core pair test, exact by construction */
-#define DBSCAN_PREC_FP16_GRAM 2  /* tcgen05 FP16 Gram product + exact recheck of the rounding band */
+#define DBSCAN_PREC_FP16_GRAM 2  /* tcgen05 FP16 Gram product, exact by proof (band 0) */
 #define DBSCAN_PREC_BF16_GRAM 3  /* tcgen05 BF16 Gram product (two-term split) + exact recheck of the band */
 
 /* Candidate generation. */
@@ -88,7 +88,10 @@ typedef struct dbscan_plan dbscan_plan;
 typedef struct dbscan_opts {
     int32_t device;      /* CUDA device ordinal */
     int32_t synchronous; /* 1: dbscan_run waits for the device and reports its errors; 0: enqueue only */
-    void *stream;        /* cudaStream_t to enqueue on; NULL = the legacy default stream */
+    void *stream;        /* cudaStream_t to enqueue on; NULL = the legacy default stream.  The
+                            eps-grid path forks independent kernels onto an internal stream of
+                            the plan and joins them back by events before the run ends, so a
+                            run stays ordered on this stream (and can be graph-captured). */
     int64_t max_n;       /* largest n this plan accepts (workspace is sized for it) */
     int32_t max_d;       /* largest d this plan accepts */
     int32_t precision;   /* DBSCAN_PREC_* */
