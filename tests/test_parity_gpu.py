@@ -354,3 +354,29 @@ def test_tensor_core_plan_reused_across_sizes():
             want_lab, want_cnt, _ = oracle.dbscan(x, eps, 6)
             np.testing.assert_array_equal(cnt.cpu().numpy(), want_cnt)
             np.testing.assert_array_equal(lab.cpu().numpy(), want_lab)
+
+
+def test_grid_run_captured_in_a_cuda_graph():
+    """An asynchronous plan's run (the eps-grid path, whose independent kernels
+    fork onto the plan's second stream and join back) captured into a CUDA graph
+    and replayed on new data of the same shape."""
+    from paper_1506_02226_gb300.api import Plan
+    a = _blobs(501, 20_000, 2, spread=12)
+    b = _blobs(502, 20_000, 2, spread=12)
+    eps, mp = 6 / 1024, 5
+    s = torch.cuda.Stream()
+    x = torch.from_numpy(a).cuda()
+    lab = torch.empty(a.shape[0], dtype=torch.int32, device="cuda")
+    with Plan(max_n=a.shape[0], max_d=2, synchronous=False, stream=s) as p:
+        with torch.cuda.stream(s):
+            p.run(x, eps, mp, labels=lab)  # warm-up outside the capture
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            p.run(x, eps, mp, labels=lab)
+        for pts in (a, b):
+            x.copy_(torch.from_numpy(pts))
+            g.replay()
+            torch.cuda.synchronize()
+            assert p.sync() == B.DBSCAN_OK
+            np.testing.assert_array_equal(lab.cpu().numpy(), oracle.dbscan(pts, eps, mp)[0])
