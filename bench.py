@@ -204,7 +204,8 @@ def algorithmic_work(name: str, n: int, d: int, gs: dict | None):
       union    per cell 32; per adjacent entry list entry, key, rep and
                centre point (28); per outer entry 12           32 C + 28 En / 12 Ef
       border   per point core flag (1) and border written (4) 5 n
-      root     per cell rep, parent and root (16)             16 C
+      root     per cell rep, parent and root (16)             16 C (also the snapshot
+               taken between the adjacent and outer-ring merges)
       label    per point index, cell, flag, cell root, border (17), label (4)  21 n
     """
     if d > 3 or gs is None:
@@ -222,6 +223,7 @@ def algorithmic_work(name: str, n: int, d: int, gs: dict | None):
         "grid_union_far": 32 * C + 12 * Ef,
         "grid_border": 5 * n,
         "grid_cell_root": 16 * C,
+        "grid_root_snapshot": 16 * C,
         "grid_label": 21 * n,
     }
     if name in table:

@@ -485,7 +485,8 @@ __global__ void __launch_bounds__(256, 6) grid_count_kernel(PairArgs a, int min_
 // (coalesced loads) and runs the lanes over the larger cell against them.
 template <int D>
 __global__ void __launch_bounds__(256) grid_union_kernel(PairArgs a, const uint8_t *__restrict__ score, int *parent,
-                                                         unsigned *status, bool far_ring) {
+                                                         unsigned *status, bool far_ring,
+                                                         const int *__restrict__ croot) {
     __shared__ float4 ybuf[8][128];
     __shared__ uint8_t ycore[8][128];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -503,6 +504,7 @@ __global__ void __launch_bounds__(256) grid_union_kernel(PairArgs a, const uint8
         const int k_begin = far_ring ? (nc >> 16) : 0, k_end = far_ring ? (nc & 0xffff) : (nc >> 16);
         const bool use_mid = !far_ring;
         const float4 mA = use_mid ? a.cell_mid[A] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int crA = croot ? croot[A] : -1;
         const float cmA = a.g.Tp1 + mA.w, mx2 = 2.f * mA.x, my2 = 2.f * mA.y, mz2 = 2.f * mA.z;
         for (int k0 = k_begin; k0 < k_end; k0 += 32) {
             const int k = k0 + lane;
@@ -510,6 +512,8 @@ __global__ void __launch_bounds__(256) grid_union_kernel(PairArgs a, const uint8
             const int repB = (B >= 0 && a.cell_key[B] > keyA) ? a.cell_rep[B] : DB_NONE;
             const float4 mB = (use_mid && repB != DB_NONE) ? a.cell_mid[B] : make_float4(0.f, 0.f, 0.f, -1e30f);
             bool need = repB != DB_NONE;
+            // cells whose snapshot roots agree are in one set already (sets only merge)
+            if (need && croot) need = croot[B] != crA;
             if (need) need = db::uf_find(parent, repA) != db::uf_find(parent, repB);
             // the two central core points first: a hit unites at once, lanes in parallel
             const bool hit = need && use_mid && is_nbr<D>(cmA, mx2, my2, mz2, mB);
@@ -637,6 +641,7 @@ __global__ void __launch_bounds__(256) grid_border_kernel(PairArgs a, int min_pt
 
 // Root of every cell with cores, once per cell (a thread per cell), and the
 // number of clusters: a cluster's root is the representative of its own cell.
+// With ctr == null it only takes a snapshot of the roots (for the outer ring).
 __global__ void grid_cell_root_kernel(const unsigned long long *ctr0, const int *__restrict__ cell_rep, int *parent,
                                       int *__restrict__ cell_root, unsigned long long *ctr) {
     __shared__ int red[8];
@@ -651,6 +656,7 @@ __global__ void grid_cell_root_kernel(const unsigned long long *ctr0, const int 
         }
         cell_root[A] = root;
     }
+    if (!ctr) return;  // a snapshot only (block-uniform)
     for (int o = 16; o > 0; o >>= 1) nr += __shfl_xor_sync(FULL, nr, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nr;
     __syncthreads();
@@ -763,10 +769,19 @@ cudaError_t grid_pair_passes(const DbWork &w, const GridGeom &g, int n, int min_
     cudaStream_t s2 = fork(w, st, 2);
     grid_border_kernel<D><<<wgrid, 256, 0, s2>>>(a, min_pts, w.score, w.border);
     w.marks->kernel("grid_border", s2);
-    grid_union_kernel<D><<<wgrid, 256, 0, st>>>(a, w.score, w.parent, w.status, false);
+    grid_union_kernel<D><<<wgrid, 256, 0, st>>>(a, w.score, w.parent, w.status, false, nullptr);
     w.marks->kernel("grid_union_near", st);
     if (g.noff > g.nnear) {
-        grid_union_kernel<D><<<wgrid, 256, 0, st>>>(a, w.score, w.parent, w.status, true);
+        // With a wide outer ring (3-D: 98 offsets), the roots after the adjacent
+        // merge (into the hash counts, free after the cells kernel) let it skip
+        // the cell pairs already joined without two finds each.
+        const int *croot = nullptr;
+        if (g.noff - g.nnear > 32) {
+            grid_cell_root_kernel<<<152 * 4, 256, 0, st>>>(w.ctr, w.cell_rep, w.parent, w.hcount, nullptr);
+            w.marks->kernel("grid_root_snapshot", st);
+            croot = w.hcount;
+        }
+        grid_union_kernel<D><<<wgrid, 256, 0, st>>>(a, w.score, w.parent, w.status, true, croot);
         w.marks->kernel("grid_union_far", st);
     }
     join(w, st, s2, 3);
