@@ -669,6 +669,17 @@ def run_ours(args, wl_name):
         alu = 3.0 * pairs / (avg[dom] * 1e-3) / 1e12
         roof["epilogue_fp32"] = {"ops_per_pair": 3, "achieved": alu, "peak": fp32_peak, "unit": "T ops/s",
                                  "frac": alu / fp32_peak}
+    elif dom in ("ap_count", "ap_union", "ap_border"):
+        # CUDA-core all-pairs tile: d+2 (Gram form, d <= 8) or 2d+1 (direct form)
+        # FP32-pipe operations per pair against SMs x 128 lanes x clock
+        nc = st0["n_core"]
+        pairs = {"ap_count": n * n, "ap_union": nc * nc / 2, "ap_border": (n - nc) * nc}[dom]
+        ops = pairs * pair_ops(d)
+        fp32_peak, _ = fp32_peak_tops()
+        ach = ops / (avg[dom] * 1e-3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "T FP32-pipe ops/s",
+                "frac": ach / fp32_peak, "traffic": None, "peak_src": "SMs x 128 lanes x max clock",
+                "ops_per_pair": pair_ops(d), "avg_ms": avg[dom]}
     elif bound == "hbm" and work:
         ach = work / (avg[dom] * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
