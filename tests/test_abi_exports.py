@@ -62,3 +62,25 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(binding.dbscan_stats) == 96
     assert ctypes.sizeof(binding.dbscan_instance) == 40
     assert binding.dbscan_instance.labels_out.offset == 32
+
+
+def test_header_is_plain_c(tmp_path):
+    """The boundary is usable from C: the header compiles as C11 with warnings
+    as errors (pedantic), and its struct sizes are the ones the binding marshals."""
+    import shutil
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi_check.c"
+    src.write_text(
+        '#include "dbscan.h"\n'
+        "_Static_assert(sizeof(dbscan_opts) == 72, \"opts\");\n"
+        "_Static_assert(sizeof(dbscan_stats) == 96, \"stats\");\n"
+        "_Static_assert(sizeof(dbscan_instance) == 40, \"instance\");\n"
+        "int use(dbscan_plan *p, const float *x, int32_t *l) {\n"
+        "    dbscan_opts o; dbscan_opts_default(&o);\n"
+        "    return dbscan_run(p, x, 0, 2, 0.1f, 5, l, (dbscan_stats *)0);\n"
+        "}\n")
+    inc = os.path.join(os.path.dirname(__file__), "..", "include")
+    r = subprocess.run(["gcc", "-std=c11", "-pedantic", "-Wall", "-Wextra", "-Werror", "-fsyntax-only", "-I", inc, str(src)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
