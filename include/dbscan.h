@@ -59,7 +59,8 @@ extern "C" {
 #define DBSCAN_ERR_CUDA 4          /* a CUDA runtime call failed */
 #define DBSCAN_ERR_TIMEOUT 5       /* a bounded device-side wait or a host wait expired */
 #define DBSCAN_ERR_BUSY 6          /* serve admission is full (slots or HBM budget) */
-#define DBSCAN_ERR_UNSUPPORTED 7   /* option or shape this build does not handle */
+#define DBSCAN_ERR_UNSUPPORTED 7   /* option or shape this build does not handle; also n above 2^29 on the
+                                      eps-grid path or above 2^25 on the all-pairs paths (int32 index ranges) */
 #define DBSCAN_ERR_NOT_FOUND 8     /* unknown serve job id */
 
 /* Pair-test arithmetic. */
@@ -222,7 +223,9 @@ typedef struct dbscan_instance {
  * tile, column chunk) items.  The first call autotunes the chunk size and grid
  * on the given batch.  Uses its own device workspace, grown on demand and kept
  * by the plan.  Synchronous; per_inst (host, nullable, `count` entries)
- * receives per-instance counts. */
+ * receives per-instance counts.  DBSCAN_ERR_ARG above 2^30 points in all;
+ * DBSCAN_ERR_UNSUPPORTED when the work items (64-point row tiles x column
+ * chunks, about n^2 / 16,384 per instance) exceed 2^31. */
 int dbscan_batch(dbscan_plan *plan, const dbscan_instance *inst, int32_t count, dbscan_stats *per_inst);
 
 /* The configuration dbscan_batch's autotuner picked for this plan on its first

@@ -148,6 +148,11 @@ int plan_run(dbscan_plan *plan, const float *points, int64_t n, int32_t d, float
     const int64_t T = (int64_t)std::floor(e * e * 1048576.0);  // exact: 48-bit square, power-of-two scale
     if (stats) stats->threshold = T;
     if (n == 0) return DBSCAN_OK;
+    // Index ranges counted in int32: the eps-grid's hash (at least 2n slots)
+    // and the all-pairs work items (row tiles x column chunks).
+    constexpr int64_t kGridMaxN = int64_t(1) << 29, kAllPairsMaxN = int64_t(1) << 25;
+    const bool grid_path = d <= 3 && o.grid != DBSCAN_GRID_OFF && plan->w.hcap > 0;
+    if (grid_path ? n > kGridMaxN : n > kAllPairsMaxN) return DBSCAN_ERR_UNSUPPORTED;
     const int64_t Dmax = (int64_t)d * 1023 * 1023;
     const int64_t Tc = std::min(T, Dmax);  // same predicate: no pair is farther than Dmax
 

@@ -430,6 +430,14 @@ extern "C" int dbscan_batch(dbscan_plan *plan, const dbscan_instance *inst, int3
         total += in.n;
     }
     if (total > INT32_MAX / 2) return DBSCAN_ERR_ARG;
+    // work items (instance, row tile, column chunk) are counted in int32: the
+    // smallest chunk gives the most items
+    int64_t items = 0;
+    for (int i = 0; i < count; ++i) {
+        const int64_t tiles = (inst[i].n + 63) / 64;
+        items += tiles * ((tiles + kCH[0] - 1) / kCH[0]);
+    }
+    if (items > INT32_MAX) return DBSCAN_ERR_UNSUPPORTED;
     int cur = -1;
     cudaGetDevice(&cur);
     if (cur != plan->opts.device) cudaSetDevice(plan->opts.device);
