@@ -5,17 +5,21 @@
 
 A step is one full clustering (prep, pair test + count -> core flags, union,
 border, labels) of one synthetic instance already resident in HBM.  The
-default workload is n = 500,000 points in d = 2 (50 Gaussian blobs with sigma
+default run measures n = 500,000 points in d = 2 (50 Gaussian blobs with sigma
 log-uniform in [0.002, 0.02] plus 20% noise, eps = 0.005, min_pts = 10), which
-runs on the eps-grid path.
+runs on the eps-grid path, and adds compact records of the other workloads
+(the same recipe in 3-D, the d = 64 precision form on FP16 and BF16 tensor
+cores, the 4,096-instance batch and the served job stream) under
+"subrecords".  --workload NAME prints the full record of one workload.
 
-Metric: G pair-tests/s, where the pair tests of a step are the ordered
-candidate pairs of the instance's eps-grid (every (p, q) with q in a cell of
-p's neighbourhood), a fixed property of the input; the same count is the unit
-of the CPU baseline, so the two are comparable.  The L2 is flushed (a 256 MiB
-write) before every timed step; each step is timed with CUDA events on the
-plan's stream.  With N > 1 (torchrun) every rank runs its own replica on its
-own GPU (the path does not shard) and the value is the sum over ranks.
+Metric: G pair-tests/s, the pair predicates D(p,q) <= T the device evaluated
+(its per-pass counters, read after every timed step) per second.  Pairs the
+method decides without a test (inside a clique cell of the eps-grid, after an
+early exit) are not counted; the eps-grid's candidate pairs are reported
+beside it.  The L2 is flushed (a 256 MiB write) before every timed step; each
+step is timed with CUDA events on the plan's stream.  With N > 1 (torchrun)
+every rank runs its own replica on its own GPU (the path does not shard) and
+the value is the sum over ranks.
 """
 from __future__ import annotations
 
@@ -261,6 +265,12 @@ def whole_job_rate(units_per_rank: float, world: int, ms_per_step: float) -> flo
 
 
 # ------------------------------------------------------------------ arms
+# Device counters 16..19 of a plan: pair tests of the count, merge, border and
+# outer-ring merge passes; the kernels that evaluate pairs, by pass.
+PASS_OF = {"grid_count": 0, "grid_union_near": 1, "grid_border": 2, "grid_union_far": 3,
+           "ap_count": 0, "ap_union": 1, "ap_border": 2, "tc_count": 0, "tc_union": 1, "tc_border": 2}
+
+
 def run_reference(args, wl_name):
     """The oracle (plain CPU brute force) timed on bounded samples of the workload."""
     import oracle
@@ -276,7 +286,7 @@ def run_reference(args, wl_name):
     t_cal = max(time.perf_counter() - t0, 1e-3)
     target = min(10.0, 120.0 / (args.warmup + args.steps))
     m = int(min(inst.n, max(2000, m0 * math.sqrt(target / t_cal))))
-    times, units = [], []
+    times, units, pts = [], [], []
     for step in range(args.warmup + args.steps):
         sub = inputs.subsample(inst, m, seed=step)
         t0 = time.perf_counter()
@@ -284,15 +294,18 @@ def run_reference(args, wl_name):
         dt = time.perf_counter() - t0
         if step >= args.warmup:
             times.append(dt)
-            units.append(work_units(sub.points, sub.eps, sub.d))
+            units.append(sub.n * sub.n)  # brute force evaluates every ordered pair
+            pts.append(sub.n)
     value = sum(units) / sum(times) / 1e9
     ms = 1e3 * sum(times) / len(times)
-    sample = f"oracle on {m}-point uniform subsamples of the {desc} workload, one per step"
+    sample = (f"oracle on {m}-point uniform subsamples of the {desc} workload, one per step; it evaluates all "
+              f"m^2 ordered pairs")
     print(json.dumps({
         "impl": "reference", "metric": "G pair-tests/s", "value": value, "unit": "G pair-tests/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": wl_name + ": " + desc, "sample_points": m},
+        "points_per_s": sum(pts) / sum(times),
         "cpu_baseline": {"value": value, "unit": "G pair-tests/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "G pair-tests/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -300,6 +313,8 @@ def run_reference(args, wl_name):
 
 
 def cpu_baseline(inst, wl_name, desc):
+    """The oracle as it stands on a bounded subsample, all host cores and one thread.
+    Brute force evaluates every ordered pair, so its rate is m^2 / time."""
     import oracle
     m = min(CPU_SAMPLE[wl_name], inst.n)
     sub = inputs.subsample(inst, m, seed=12345)
@@ -307,24 +322,232 @@ def cpu_baseline(inst, wl_name, desc):
     t0 = time.perf_counter()
     oracle.dbscan(sub.points, sub.eps, sub.min_pts, nthreads=cores)
     dt = time.perf_counter() - t0
-    units = work_units(sub.points, sub.eps, sub.d)
-    # the same oracle on one thread, on a sample a quarter the size (brute force
-    # and the candidate count both scale as n^2, so the rate compares)
     m1 = max(m // 4, min(m, 1000))
     sub1 = inputs.subsample(inst, m1, seed=12345)
     t1 = time.perf_counter()
     oracle.dbscan(sub1.points, sub1.eps, sub1.min_pts, nthreads=1)
     dt1 = time.perf_counter() - t1
-    units1 = work_units(sub1.points, sub1.eps, sub1.d)
-    return {"value": units / dt / 1e9, "unit": "G pair-tests/s", "cores": cores, "kind": "oracle",
+    return {"value": m * m / dt / 1e9, "unit": "G pair-tests/s", "cores": cores, "kind": "oracle",
+            "points_per_s": m / dt,
             "sample": f"full oracle run on a {m}-point uniform subsample of the {desc} workload "
-                      f"({units} pair tests, {dt:.2f} s)",
-            "single_thread": {"value": units1 / dt1 / 1e9, "cores": 1,
-                              "sample": f"{m1}-point subsample ({units1} pair tests, {dt1:.2f} s)"}}
+                      f"({m * m} pair tests, all ordered pairs, {dt:.2f} s)",
+            "single_thread": {"value": m1 * m1 / dt1 / 1e9, "cores": 1, "points_per_s": m1 / dt1,
+                              "sample": f"{m1}-point subsample ({m1 * m1} pair tests, {dt1:.2f} s)"}}
 
 
-def run_batch(args):
+def roofline(dom: str, avg_ms: float, ev: list, n: int, d: int, gs, wl_name: str, traffic):
+    """Roofline of the dominant kernel from its CUDA-event time and the pairs it evaluated.
+
+    Pair kernels: the tensor-core passes against the measured bf16 peak (2K FLOPs
+    per pair, K = d padded to 16) with the epilogue's ~3 FP32 operations per pair
+    beside it; CUDA-core pair kernels (all-pairs tile and the eps-grid's count,
+    merge and border) against the FP32 pipe at d+2 (Gram form) or 2d+1 (direct
+    form) operations per evaluated pair, with the eps-grid kernels' HBM
+    fraction beside it.  Other kernels against HBM."""
+    peaks = load_peaks()
+    sec = avg_ms * 1e-3
+    if dom in PASS_OF:
+        pairs = ev[PASS_OF[dom]]
+        if dom.startswith("tc_"):
+            K = -(-d // 16) * 16
+            flops = 2.0 * pairs * K
+            ach = flops / sec / 1e12
+            roof = {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"],
+                    "unit": "TFLOP/s", "frac": ach / peaks["bf16_tflops"], "traffic": traffic,
+                    "peak_src": peaks["src"] + " bf16 burst (FP16 dense rate is the same)",
+                    "algorithmic_flops": flops, "pairs": pairs, "avg_ms": avg_ms}
+            fp32_peak, _ = fp32_peak_tops()
+            alu = 3.0 * pairs / sec / 1e12
+            roof["epilogue_fp32"] = {"ops_per_pair": 3, "achieved": alu, "peak": fp32_peak, "unit": "T ops/s",
+                                     "frac": alu / fp32_peak}
+            return roof
+        ops_pp = pair_ops(d) if not dom.startswith("grid_") else d + 2
+        fp32_peak, sms = fp32_peak_tops()
+        ach = pairs * ops_pp / sec / 1e12
+        alu = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "T FP32-pipe ops/s",
+               "frac": ach / fp32_peak, "traffic": traffic, "peak_src": f"{sms} SMs x 128 lanes x max SM clock",
+               "pairs": pairs, "ops_per_pair": ops_pp, "avg_ms": avg_ms}
+        bound, work = algorithmic_work(dom, n, d, gs)
+        if bound != "hbm" or not work:
+            return alu
+        # The eps-grid pair kernels move more bytes than they compute: the bound is
+        # the larger of the two roofline times (FP32 ops / FP32 peak, bytes / HBM peak).
+        gbs = work / sec / 1e9
+        hbm = {"kernel": dom, "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+               "frac": gbs / peaks["hbm_gbs"], "traffic": traffic if traffic is not None else ncu_traffic(wl_name, dom),
+               "peak_src": peaks["src"], "algorithmic_bytes": work, "pairs": pairs, "avg_ms": avg_ms}
+        t_alu = pairs * ops_pp / (fp32_peak * 1e12)
+        t_hbm = work / (peaks["hbm_gbs"] * 1e9)
+        main, other = (hbm, alu) if t_hbm >= t_alu else (alu, hbm)
+        main["other_bound"] = {k: other[k] for k in ("bound", "achieved", "peak", "unit", "frac")}
+        main["roofline_times_us"] = {"alu": t_alu * 1e6, "hbm": t_hbm * 1e6}
+        return main
+    bound, work = algorithmic_work(dom, n, d, gs)
+    if bound == "hbm" and work:
+        ach = work / sec / 1e9
+        return {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": traffic if traffic is not None else ncu_traffic(wl_name, dom),
+                "peak_src": peaks["src"], "algorithmic_bytes": work, "avg_ms": avg_ms}
+    return {"kernel": dom, "bound": bound, "achieved": None, "peak": None, "unit": None, "frac": None,
+            "traffic": None, "avg_ms": avg_ms}
+
+
+def run_ours(args, wl_name, baseline=True, steps=None):
+    """Full record of one single-instance workload (dbscan_run on device buffers)."""
+    from paper_1506_02226_gb300 import build as cuda_build
+    cuda_build.build()  # in-tree, only recompiles what changed
+    import torch
+    from paper_1506_02226_gb300 import binding as B
+    from paper_1506_02226_gb300.api import Plan
+
+    steps = steps or args.steps
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        if not tdist.is_initialized():
+            tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = tdist
+
+    desc, make = WORKLOADS[wl_name]
+    inst = make()
+    if args.n and args.n < inst.n:  # smaller sample of the same recipe (profiler captures)
+        inst = inputs.subsample(inst, args.n, seed=0)
+        desc = f"{args.n}-point uniform subsample of the {desc} workload"
+    n, d = inst.n, inst.d
+    x = torch.from_numpy(inst.points).cuda()
+    labels = torch.empty(n, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    prec = PRECISION.get(wl_name, 0)
+    # one synchronous run for the statistics (and the launch count)
+    with Plan(max_n=n, max_d=d, precision=prec) as p:
+        _, st0 = p.run(x, inst.eps, inst.min_pts, stats=True)
+    candidates = st0["candidate_pairs"]
+    gs = None
+    if st0["path"] == B.DBSCAN_PATH_GRID:
+        gs = grid_structure(inst.points, inst.eps)
+        if gs["candidate_pairs"] != candidates:
+            raise RuntimeError(f"candidate-pair count mismatch: device {candidates} host {gs['candidate_pairs']}")
+
+    # Timed steps run without per-kernel marks, so the grid path's independent
+    # kernels may overlap on its second stream; per-kernel times come from a
+    # separate profiled plan that runs them one after another.
+    plan = Plan(max_n=n, max_d=d, synchronous=False, stream=stream, profile=False, precision=prec)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    step_ms, step_pairs = [], []
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            plan.run(x, inst.eps, inst.min_pts, labels=labels)
+        if plan.sync() != 0:
+            raise RuntimeError("warm-up run reported an error")
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        time.sleep(0.3)
+        for _ in range(steps):
+            flush.fill_(1)  # evict the 129 MB L2 before the timed step
+            ev0.record(stream)
+            plan.run(x, inst.eps, inst.min_pts, labels=labels)
+            ev1.record(stream)
+            ev1.synchronize()
+            step_ms.append(ev0.elapsed_time(ev1))
+            step_pairs.append(sum(plan.pair_tests()))  # this step's device counters (outside the events)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+    if plan.sync() != 0:
+        raise RuntimeError("timed run reported an error")
+    kern: dict[str, list[float]] = {}
+    ev_runs = []
+    pplan = Plan(max_n=n, max_d=d, synchronous=False, stream=stream, profile=True, precision=prec)
+    with torch.cuda.stream(stream):
+        for r in range(3 + max(5, min(steps, 30))):
+            flush.fill_(1)
+            pplan.run(x, inst.eps, inst.min_pts, labels=labels)
+            stream.synchronize()
+            if r >= 3:
+                for nm, ms in pplan.phase_times():
+                    kern.setdefault(nm, []).append(ms)
+                ev_runs.append(pplan.pair_tests())
+    if pplan.sync() != 0:
+        raise RuntimeError("profiled run reported an error")
+    pplan.close()
+    total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
+    if dist:
+        dist.barrier()
+    ms_per_step = total_ms / steps
+    pairs_per_step = statistics.mean(step_pairs)
+    value = whole_job_rate(pairs_per_step, world, ms_per_step) / 1e9
+
+    # end to end: host (pinned) buffers through the C ABI, copies inside the timed region
+    host_pts = torch.from_numpy(inst.points).pin_memory()
+    host_lab = torch.empty(n, dtype=torch.int32).pin_memory()
+    eplan = Plan(max_n=n, max_d=d, stream=stream, precision=prec)
+    for _ in range(2):
+        eplan.run_host(host_pts, inst.eps, inst.min_pts, labels=host_lab)
+    e2e_s = []
+    for _ in range(max(3, steps // 4) if not args.no_baseline else 1):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        eplan.run_host(host_pts, inst.eps, inst.min_pts, labels=host_lab)
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_ms = 1e3 * statistics.mean(e2e_s)
+    eplan.close()
+    plan.close()
+
+    if rank != 0:
+        return None
+    avg = {k: statistics.mean(v) for k, v in kern.items()}
+    ev_pass = [statistics.mean(r[k] for r in ev_runs) for k in range(4)]
+    dom = max(avg, key=avg.get)
+    roof = roofline(dom, avg[dom], ev_pass, n, d, gs, wl_name, args.traffic)
+    others = {}
+    for k in sorted(avg, key=avg.get, reverse=True)[1:4]:
+        if k in PASS_OF and ev_pass[PASS_OF[k]] > 0:
+            r = roofline(k, avg[k], ev_pass, n, d, gs, wl_name, None)
+            others[k] = {"bound": r["bound"], "frac": r["frac"], "achieved": r["achieved"], "unit": r["unit"],
+                         "pairs": r.get("pairs"), "avg_ms": avg[k]}
+    cpu = cpu_baseline(inst, wl_name, desc) if (baseline and not args.no_baseline) else None
+    return {
+        "metric": "G pair-tests/s", "value": value, "unit": "G pair-tests/s", "n_gpus": world,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": {2: "f32", 3: "f16" if prec != 3 else "bf16"}.get(
+            st0["path"], "f32"), "data": "synthetic",
+        "config": {"workload": wl_name + ": " + desc, "n": n, "d": d, "eps": inst.eps, "min_pts": inst.min_pts,
+                   "path": {1: "eps-grid", 2: "all-pairs SIMT", 3: "all-pairs tensor-core"}.get(st0["path"]),
+                   "l2": "flushed by a 256 MiB write before every timed step", "parallelism": f"replicas x{world}"},
+        "pair_tests_per_step": pairs_per_step,
+        "pair_tests_by_pass": dict(zip(["count", "merge", "border", "merge_outer_ring"], ev_pass)),
+        "pair_tests_note": "pair predicates the device evaluated (its per-pass counters), averaged over the "
+                           "timed steps; pairs decided without a test are not counted",
+        "candidate_pairs_per_step": candidates if st0["path"] == B.DBSCAN_PATH_GRID else n * n,
+        "evaluated_vs_min": pairs_per_step / max(n * (n - 1) / 2, 1),
+        "band_pairs_per_step": st0["band_pairs"],
+        "points_per_s": world * n / (ms_per_step * 1e-3),
+        "clusters": st0["n_clusters"], "core": st0["n_core"], "noise": st0["n_noise"],
+        "kernels_ms": {k: round(v, 5) for k, v in sorted(avg.items(), key=lambda kv: -kv[1])},
+        "kernels_ms_note": "each kernel alone (a profiled run, kernels serialised, L2 flushed before each run)",
+        "roofline": roof,
+        "roofline_next": others,
+        "cpu_baseline": cpu,
+        "e2e": {"value": pairs_per_step / (e2e_ms * 1e-3) / 1e9, "unit": "G pair-tests/s", "ms_per_step": e2e_ms,
+                "points_per_s": n / (e2e_ms * 1e-3), "h2d_bytes_per_step": 4 * n * d, "d2h_bytes_per_step": 4 * n},
+        "gpu_launches": st0["kernels"] * steps,
+        "clocks": clk,
+    }
+
+
+def run_batch(args, steps=None):
     """4,096 independent instances per step, one dbscan_batch call (graph launch)."""
+    steps = steps or args.steps
     from paper_1506_02226_gb300 import build as cuda_build
     cuda_build.build()
     import torch
@@ -361,6 +584,8 @@ def run_batch(args):
         raise RuntimeError("dbscan_batch failed")
     ch, bps = B.dbscan_batch_config(plan.handle)
     ncore = [st[k].n_core for k in range(count)]
+    pair_tests = sum(st[k].pair_tests for k in range(count))  # device counters of that call
+    pass_pairs = B.dbscan_plan_counters(plan.handle)[16:19]  # that call's totals per pass
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -368,7 +593,7 @@ def run_batch(args):
         clocks = ClockSampler(torch.cuda.current_device())
         time.sleep(0.3)
         step_ms = []
-        for _ in range(args.steps):
+        for _ in range(steps):
             flush.fill_(1)
             ev0.record(stream)
             if B.dbscan_batch(plan.handle, arr) != 0:
@@ -386,7 +611,7 @@ def run_batch(args):
         # the same instances through a loop of single-instance launches
         single = Plan(max_n=8192, max_d=16, stream=stream, synchronous=False)
         loop_ms = []
-        for _ in range(max(2, args.steps // 10)):
+        for _ in range(max(2, steps // 10)):
             flush.fill_(1)
             ev0.record(stream)
             for k, inst in enumerate(insts):
@@ -400,7 +625,7 @@ def run_batch(args):
         # end to end: host buffers in, labels out, every step
         harr = table(x.data_ptr(), lab.data_ptr())
         e2e = []
-        for _ in range(max(3, args.steps // 4)):
+        for _ in range(max(3, steps // 4)):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             x.copy_(host_pts, non_blocking=True)
@@ -415,12 +640,12 @@ def run_batch(args):
     peak_tops, sms = fp32_peak_tops()
     dom = max(kern, key=kern.get)
     if dom in ("batch_count", "batch_union", "batch_border"):
-        if dom == "batch_count":
-            ops = sum(i.n * i.n * pair_ops(i.d) for i in insts)
-        elif dom == "batch_union":
-            ops = sum(c * c / 2 * pair_ops(i.d) for i, c in zip(insts, ncore))
-        else:
-            ops = sum((i.n - c) * i.n * pair_ops(i.d) for i, c in zip(insts, ncore))
+        # pairs each pass evaluated (device counters of a batch run with statistics)
+        # times the FP32-pipe operations of one pair test at the instance's d
+        k = ("batch_count", "batch_union", "batch_border").index(dom)
+        pp = pass_pairs[k]
+        mean_ops = sum(i.n * i.n * pair_ops(i.d) for i in insts) / max(sum(i.n * i.n for i in insts), 1)
+        ops = pp * mean_ops
         ach = ops / (kern[dom] * 1e-3) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak_tops, "unit": "T FP32-pipe ops/s",
                 "frac": ach / peak_tops, "traffic": args.traffic, "peak_src": f"{sms} SMs x 128 lanes x max clock",
@@ -441,33 +666,36 @@ def run_batch(args):
                "sample": f"the first {len(sample)} of the {count} instances, run one after another ({dt:.2f} s)"}
     e2e_ms = 1e3 * statistics.mean(e2e)
     out = {
-        "metric": "batched jobs/s", "value": jobs, "unit": "jobs/s", "n_gpus": 1, "steps": args.steps,
+        "metric": "batched jobs/s", "value": jobs, "unit": "jobs/s", "n_gpus": 1, "steps": steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"batch: {count} instances, n log-uniform 64..8192, d in {{2,3,16}}, 1-8 blobs + 10% "
                                "noise, eps U[0.01,0.05], min_pts U{4..16}", "points": int(loffs[-1]),
                    "path": "all-pairs SIMT, one graph launch", "autotuned": {"chunk_tiles": ch, "blocks_per_sm": bps},
                    "l2": "flushed by a 256 MiB write before every timed step"},
-        "pair_tests_per_step": pairs, "pair_tests_per_s": pairs / (ms * 1e-3),
+        "pair_tests_per_step": pair_tests, "pair_tests_per_s": pair_tests / (ms * 1e-3),
+        "all_pairs_per_step": pairs,
         "launch_loop": {"jobs_per_s": count / (statistics.mean(loop_ms) * 1e-3), "ms": statistics.mean(loop_ms),
                         "what": "the same instances, one dbscan_run per instance on one stream"},
         "kernels_ms": {k: round(v, 5) for k, v in sorted(kern.items(), key=lambda kv: -kv[1])},
         "roofline": roof, "cpu_baseline": cpu,
         "e2e": {"value": count / (e2e_ms * 1e-3), "unit": "jobs/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": 4 * int(offs[-1]), "d2h_bytes_per_step": 4 * int(loffs[-1])},
-        "gpu_launches": 6 * args.steps, "clocks": clk,
+        "gpu_launches": 6 * steps, "clocks": clk,
     }
-    print(json.dumps(out))
+    return out
 
 
 def run_serve(args):
     """Jobs through the server: closed-loop saturation, then Poisson arrivals at
-    0.7x and 0.9x of it, with per-job submit-to-done latency."""
+    0.7x and 0.9x of it, with per-job submit-to-done latency; beside it the same
+    jobs through a plain loop of dbscan_run calls on one stream."""
     from paper_1506_02226_gb300 import build as cuda_build
     cuda_build.build()
     import threading
     import torch
     from paper_1506_02226_gb300 import binding as B
+    from paper_1506_02226_gb300.api import Plan
 
     pool = [inputs.serve_job(i) for i in range(args.serve_pool)]
     dev = []
@@ -478,12 +706,33 @@ def run_serve(args):
         s.points, s.n, s.d, s.eps, s.min_pts, s.labels_out = x.data_ptr(), inst.n, inst.d, inst.eps, inst.min_pts, \
             lab.data_ptr()
         dev.append((x, lab, s))
+    max_n = max(i.n for i in pool)
+    njobs = args.serve_jobs
+
+    # the plain loop: one plan sized for the largest job, one stream, one
+    # dbscan_run per job in submission order, waited for at the end
+    stream = torch.cuda.Stream()
+    loop_jobs = min(njobs, args.serve_loop_jobs)
+    with Plan(max_n=max_n, max_d=64, synchronous=False, stream=stream) as single:
+        for k in range(min(len(dev), 16)):  # warm-up (first launches of every kernel)
+            s = dev[k][2]
+            B.dbscan_run(single.handle, s.points, s.n, s.d, s.eps, s.min_pts, s.labels_out)
+        if single.sync() != 0:
+            raise RuntimeError("launch loop warm-up failed")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(loop_jobs):
+            s = dev[k % len(dev)][2]
+            B.dbscan_run(single.handle, s.points, s.n, s.d, s.eps, s.min_pts, s.labels_out)
+        if single.sync() != 0:
+            raise RuntimeError("launch loop failed")
+        loop_s = time.perf_counter() - t0
+
     o = B.dbscan_serve_opts_default()
     o.slots = args.serve_slots
-    o.max_n = max(i.n for i in pool)
+    o.max_n = max_n
     o.max_d = 64
     srv = B.dbscan_serve_create(o)
-    njobs = args.serve_jobs
 
     def run(arrivals):
         ids, lats = [None] * njobs, [0.0] * njobs
@@ -522,235 +771,102 @@ def run_serve(args):
                              "p50_ms": float(np.percentile(lats, 50)) / 1e3,
                              "p99_ms": float(np.percentile(lats, 99)) / 1e3}
     clk = clocks.stop()
+    info = B.dbscan_serve_info(srv) if hasattr(B, "dbscan_serve_info") else None
     B.dbscan_serve_destroy(srv)
     mix = {d: sum(1 for i in pool if i.d == d) for d in (2, 3, 32)}
-    out = {
+    return {
         "metric": "served jobs/s", "value": sat, "unit": "jobs/s", "n_gpus": 1, "steps": njobs, "warmup":
             min(len(dev), 2 * args.serve_slots), "ms_per_step": 1e3 / sat, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"serve: {njobs} jobs drawn cyclically from {len(pool)} seeded jobs, n log-uniform "
                                f"1k..500k, d in {{2,3,32}} ({mix}), blob+noise, per-job eps/min_pts",
-                   "slots": args.serve_slots, "hbm_budget_gib": 120,
-                   "admission": "slot-bound: every job's footprint is far below the budget"},
+                   "slots": args.serve_slots, "hbm_budget_gib": o.hbm_budget_bytes / 2 ** 30},
         "closed_loop": {"jobs_per_s": sat, "p50_ms": float(np.percentile(lat_closed, 50)) / 1e3,
-                        "p99_ms": float(np.percentile(lat_closed, 99)) / 1e3},
+                        "p99_ms": float(np.percentile(lat_closed, 99)) / 1e3,
+                        "note": "all jobs submitted at once: latency includes queueing behind the whole stream"},
         "poisson": levels,
+        "launch_loop": {"jobs_per_s": loop_jobs / loop_s, "jobs": loop_jobs,
+                        "what": "the first jobs of the same stream, one dbscan_run per job on one stream and one "
+                                "plan sized for the largest job"},
+        "server_memory": info,
         "e2e": None, "roofline": None, "cpu_baseline": None, "gpu_launches": None, "clocks": clk,
     }
-    print(json.dumps(out))
 
 
-def run_ours(args, wl_name):
-    from paper_1506_02226_gb300 import build as cuda_build
-    cuda_build.build()  # in-tree, only recompiles what changed
-    import torch
-    from paper_1506_02226_gb300 import binding as B
-    from paper_1506_02226_gb300.api import Plan
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    desc, make = WORKLOADS[wl_name]
-    inst = make()
-    if args.n and args.n < inst.n:  # smaller sample of the same recipe (profiler captures)
-        inst = inputs.subsample(inst, args.n, seed=0)
-        desc = f"{args.n}-point uniform subsample of the {desc} workload"
-    n, d = inst.n, inst.d
-    x = torch.from_numpy(inst.points).cuda()
-    labels = torch.empty(n, dtype=torch.int32, device="cuda")
-    stream = torch.cuda.Stream()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-
-    prec = PRECISION.get(wl_name, 0)
-    # one synchronous run for the statistics (and the launch count)
-    with Plan(max_n=n, max_d=d, precision=prec) as p:
-        _, st0 = p.run(x, inst.eps, inst.min_pts, stats=True)
-    units = st0["candidate_pairs"]
-    gs = None
-    if st0["path"] == B.DBSCAN_PATH_GRID:
-        gs = grid_structure(inst.points, inst.eps)
-        host_units = gs["candidate_pairs"]
-        if host_units != units:
-            raise RuntimeError(f"candidate-pair count mismatch: device {units} host {host_units}")
-
-    # Timed steps run without per-kernel marks, so the grid path's independent
-    # kernels may overlap on its second stream; per-kernel times come from a
-    # separate profiled plan that runs them one after another.
-    plan = Plan(max_n=n, max_d=d, synchronous=False, stream=stream, profile=False, precision=prec)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    kern: dict[str, list[float]] = {}
-    step_ms = []
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            plan.run(x, inst.eps, inst.min_pts, labels=labels)
-        if plan.sync() != 0:
-            raise RuntimeError("warm-up run reported an error")
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        clocks = ClockSampler(local)
-        time.sleep(0.3)
-        for _ in range(args.steps):
-            flush.fill_(1)  # evict the 129 MB L2 before the timed step
-            ev0.record(stream)
-            plan.run(x, inst.eps, inst.min_pts, labels=labels)
-            ev1.record(stream)
-            ev1.synchronize()
-            step_ms.append(ev0.elapsed_time(ev1))
-        torch.cuda.synchronize()
-        clk = clocks.stop()
-    if plan.sync() != 0:
-        raise RuntimeError("timed run reported an error")
-    pplan = Plan(max_n=n, max_d=d, synchronous=False, stream=stream, profile=True, precision=prec)
-    with torch.cuda.stream(stream):
-        for r in range(3 + max(5, min(args.steps, 30))):
-            flush.fill_(1)
-            pplan.run(x, inst.eps, inst.min_pts, labels=labels)
-            stream.synchronize()
-            if r >= 3:
-                for nm, ms in pplan.phase_times():
-                    kern.setdefault(nm, []).append(ms)
-    if pplan.sync() != 0:
-        raise RuntimeError("profiled run reported an error")
-    pplan.close()
-    total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
-    if dist:
-        dist.barrier()
-    ms_per_step = total_ms / args.steps
-    value = whole_job_rate(units, world, ms_per_step) / 1e9
-
-    # end to end: host (pinned) buffers through the C ABI, copies inside the timed region
-    host_pts = torch.from_numpy(inst.points).pin_memory()
-    host_lab = torch.empty(n, dtype=torch.int32).pin_memory()
-    eplan = Plan(max_n=n, max_d=d, stream=stream, precision=prec)
-    for _ in range(2):
-        eplan.run_host(host_pts, inst.eps, inst.min_pts, labels=host_lab)
-    e2e_s = []
-    for _ in range(max(3, args.steps // 4) if not args.no_baseline else 1):
-        flush.fill_(1)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        eplan.run_host(host_pts, inst.eps, inst.min_pts, labels=host_lab)
-        e2e_s.append(time.perf_counter() - t0)
-    e2e_ms = 1e3 * statistics.mean(e2e_s)
-    eplan.close()
-    plan.close()
-
-    if rank != 0:
-        if dist:
-            dist.destroy_process_group()
-        return
-
-    avg = {k: statistics.mean(v) for k, v in kern.items()}
-    dom = max(avg, key=avg.get)
-    peaks = load_peaks()
-    bound, work = algorithmic_work(dom, n, d, gs)
-    if dom.startswith("tc_") and dom in ("tc_count", "tc_union", "tc_border"):
-        K = -(-d // 16) * 16
-        nc = st0["n_core"]
-        pairs = {"tc_count": n * n, "tc_union": nc * nc / 2, "tc_border": (n - nc) * nc}[dom]
-        flops = 2.0 * pairs * K
-        peak = peaks["bf16_tflops"]
-        ach = flops / (avg[dom] * 1e-3) / 1e12
-        roof = {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": args.traffic, "peak_src": peaks["src"], "algorithmic_flops": flops,
-                "avg_ms": avg[dom]}
-        # the epilogue beside the MMA: about 3 FP32 operations per pair (the exact
-        # decision and the count), against the FP32 pipe (SMs x 128 lanes x clock)
-        fp32_peak, _ = fp32_peak_tops()
-        alu = 3.0 * pairs / (avg[dom] * 1e-3) / 1e12
-        roof["epilogue_fp32"] = {"ops_per_pair": 3, "achieved": alu, "peak": fp32_peak, "unit": "T ops/s",
-                                 "frac": alu / fp32_peak}
-    elif dom in ("ap_count", "ap_union", "ap_border"):
-        # CUDA-core all-pairs tile: d+2 (Gram form, d <= 8) or 2d+1 (direct form)
-        # FP32-pipe operations per pair against SMs x 128 lanes x clock
-        nc = st0["n_core"]
-        pairs = {"ap_count": n * n, "ap_union": nc * nc / 2, "ap_border": (n - nc) * nc}[dom]
-        ops = pairs * pair_ops(d)
-        fp32_peak, _ = fp32_peak_tops()
-        ach = ops / (avg[dom] * 1e-3) / 1e12
-        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "T FP32-pipe ops/s",
-                "frac": ach / fp32_peak, "traffic": None, "peak_src": "SMs x 128 lanes x max clock",
-                "ops_per_pair": pair_ops(d), "avg_ms": avg[dom]}
-    elif bound == "hbm" and work:
-        ach = work / (avg[dom] * 1e-3) / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"],
-                "traffic": args.traffic if args.traffic is not None else ncu_traffic(wl_name, dom),
-                "peak_src": peaks["src"], "algorithmic_bytes": work, "avg_ms": avg[dom]}
-    else:
-        roof = {"kernel": dom, "bound": bound, "achieved": None, "peak": None, "unit": None, "frac": None,
-                "traffic": None, "avg_ms": avg[dom]}
-    cpu = cpu_baseline(inst, wl_name, desc) if not args.no_baseline else None
-    out = {
-        "metric": "G pair-tests/s", "value": value, "unit": "G pair-tests/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": wl_name + ": " + desc, "n": n, "d": d, "eps": inst.eps, "min_pts": inst.min_pts,
-                   "path": {1: "eps-grid", 2: "all-pairs SIMT", 3: "all-pairs tensor-core"}.get(st0["path"]),
-                   "l2": "flushed by a 256 MiB write before every timed step", "parallelism": f"replicas x{world}"},
-        "pair_tests_per_step": units,
-        # all-pairs paths: pairs the three passes evaluate (n^2 counted, cores^2/2
-        # merged, non-cores x cores bordered) over the n(n-1)/2 minimum
-        "evaluated_vs_min": (None if st0["path"] == B.DBSCAN_PATH_GRID else
-                             (n * n + st0["n_core"] ** 2 / 2 + (n - st0["n_core"]) * st0["n_core"])
-                             / max(n * (n - 1) / 2, 1)),
-        "band_pairs_per_step": st0["band_pairs"],
-        "points_per_s": world * n / (ms_per_step * 1e-3),
-        "clusters": st0["n_clusters"], "core": st0["n_core"], "noise": st0["n_noise"],
-        "kernels_ms": {k: round(v, 5) for k, v in sorted(avg.items(), key=lambda kv: -kv[1])},
-        "kernels_ms_note": "each kernel alone (a profiled run, kernels serialised, L2 flushed before each run)",
-        "roofline": roof,
-        "cpu_baseline": cpu,
-        "e2e": {"value": units / (e2e_ms * 1e-3) / 1e9, "unit": "G pair-tests/s", "ms_per_step": e2e_ms,
-                "h2d_bytes_per_step": 4 * n * d, "d2h_bytes_per_step": 4 * n},
-        "gpu_launches": st0["kernels"] * args.steps,
-        "clocks": clk,
-    }
-    print(json.dumps(out))
-    if dist:
-        dist.destroy_process_group()
+def compact(rec: dict) -> dict:
+    """The figures of a workload's record that the default line carries."""
+    keep = ("metric", "value", "unit", "ms_per_step", "dtype", "pair_tests_per_step", "candidate_pairs_per_step",
+            "evaluated_vs_min", "band_pairs_per_step", "points_per_s", "launch_loop", "closed_loop", "poisson",
+            "server_memory", "config", "clocks")
+    out = {k: rec[k] for k in keep if k in rec}
+    r = rec.get("roofline")
+    if r:
+        out["roofline"] = {k: r[k] for k in ("kernel", "bound", "achieved", "peak", "unit", "frac", "avg_ms",
+                                             "epilogue_fp32", "other_bound") if k in r}
+    if rec.get("e2e"):
+        out["e2e"] = {k: rec["e2e"][k] for k in ("value", "unit", "ms_per_step") if k in rec["e2e"]}
+    if rec.get("cpu_baseline"):
+        out["cpu_baseline"] = {k: rec["cpu_baseline"][k] for k in ("value", "unit", "cores", "sample")}
+    if "kernels_ms" in rec:
+        out["kernels_ms"] = dict(list(rec["kernels_ms"].items())[:4])
+    return out
 
 
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch", "serve"], default="lowd2")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch", "serve"], default=None,
+                    help="print the full record of one workload (default: lowd2 with the others as subrecords)")
+    ap.add_argument("--no-subrecords", action="store_true", help="default run without the other workloads")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU baseline (for profiler runs)")
     ap.add_argument("--n", type=int, default=0, help="cluster a uniform subsample of this many points instead")
     ap.add_argument("--batch-count", type=int, default=4096, help="instances of the batch workload")
     ap.add_argument("--serve-jobs", type=int, default=10_000, help="jobs of the serve workload")
     ap.add_argument("--serve-pool", type=int, default=192, help="distinct seeded jobs the serve workload cycles")
     ap.add_argument("--serve-slots", type=int, default=8, help="server slots")
+    ap.add_argument("--serve-loop-jobs", type=int, default=2000, help="jobs of the plain launch loop beside serve")
     ap.add_argument("--cpu-sample", type=int, default=128, help="instances the oracle runs for the batch baseline")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture, for the roofline")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    wl = args.workload
     if args.impl == "reference":
         if int(os.environ.get("RANK", "0")) != 0:
             return
-        run_reference(args, args.workload)
+        run_reference(args, wl or "lowd2")
         return
-    if args.workload == "batch":
-        run_batch(args)
+    if wl == "batch":
+        print(json.dumps(run_batch(args)))
         return
-    if args.workload == "serve":
-        run_serve(args)
+    if wl == "serve":
+        print(json.dumps(run_serve(args)))
         return
-    run_ours(args, args.workload)
+    if wl is not None:
+        rec = run_ours(args, wl)
+        if rec is not None:
+            print(json.dumps(rec))
+        return
+    rec = run_ours(args, "lowd2")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rec is not None and world == 1 and not args.no_subrecords:
+        sub = {}
+        sub["lowd3"] = compact(run_ours(args, "lowd3", baseline=False))
+        sub["highd_fp16"] = compact(run_ours(args, "highd", steps=min(args.steps, 10)))
+        sub["highd_bf16"] = compact(run_ours(args, "highd_bf16", baseline=False, steps=min(args.steps, 10)))
+        sub["batch"] = compact(run_batch(args, steps=min(args.steps, 10)))
+        sub["serve"] = compact(run_serve(args))
+        rec["subrecords"] = sub
+    if rec is not None:
+        print(json.dumps(rec))
+    if world > 1:
+        import torch.distributed as tdist
+        if tdist.is_initialized():
+            tdist.destroy_process_group()
 
 
 if __name__ == "__main__":

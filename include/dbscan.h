@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define DBSCAN_ABI_VERSION 1
+#define DBSCAN_ABI_VERSION 2
 
 /* Status codes. */
 #define DBSCAN_OK 0
@@ -115,7 +115,11 @@ typedef struct dbscan_stats {
     int64_t threshold;       /* T = floor(eps^2 * 2^20) */
     float ms_total;          /* device time of the run (CUDA events), when measured */
     int32_t kernels;         /* kernel launches the run enqueued */
-    float reserved_f[6];
+    int64_t pair_tests;      /* pair predicates evaluated on the device, all passes (the count, merge
+                                and border passes' counters; pairs decided without a test, such as
+                                the pairs inside a clique cell or those skipped by an early exit,
+                                are not counted) */
+    float reserved_f[4];
 } dbscan_stats;
 
 /* Fills *opts with defaults: device 0, synchronous, default stream, max_n 1<<20,
@@ -185,9 +189,12 @@ int dbscan_tc_verify(dbscan_plan *plan, const float *points, int64_t n, int32_t 
                      dbscan_tc_report *out);
 
 /* Raw device counters of the plan's last run (diagnostics): copies up to n of
- * the plan's 16 64-bit counters to out (host).  Slot 6 counts band pairs
- * rechecked exactly; builds made for pipeline diagnostics fill slots 9..13
- * with cycles spent blocked per pipeline role.  Waits for the plan's stream. */
+ * the plan's 32 64-bit counters to out (host).  Slot 6 counts band pairs
+ * rechecked exactly; slots 16..19 count the pair predicates evaluated by the
+ * count, merge, border and (eps-grid path) outer-ring merge passes (their sum
+ * is dbscan_stats.pair_tests);
+ * builds made for pipeline diagnostics fill slots 9..13 with cycles spent
+ * blocked per pipeline role.  Waits for the plan's stream. */
 int dbscan_plan_counters(dbscan_plan *plan, uint64_t *out, int32_t n);
 
 /* Device bytes the plan's workspace holds. */
@@ -225,7 +232,10 @@ typedef struct dbscan_instance {
  * by the plan.  Synchronous; per_inst (host, nullable, `count` entries)
  * receives per-instance counts.  DBSCAN_ERR_ARG above 2^30 points in all;
  * DBSCAN_ERR_UNSUPPORTED when the work items (64-point row tiles x column
- * chunks, about n^2 / 16,384 per instance) exceed 2^31. */
+ * chunks, about n^2 / 16,384 per instance) exceed 2^31.  With per_inst given,
+ * each entry's pair_tests counts the instance's evaluated pair predicates and
+ * the plan's counters 16..18 (dbscan_plan_counters) hold the batch's totals
+ * for the count, merge and border passes. */
 int dbscan_batch(dbscan_plan *plan, const dbscan_instance *inst, int32_t count, dbscan_stats *per_inst);
 
 /* The configuration dbscan_batch's autotuner picked for this plan on its first
@@ -274,7 +284,11 @@ int dbscan_serve_poll(dbscan_server *srv, uint64_t job_id, int32_t *done);
  * job's status.  Thread-safe. */
 int dbscan_serve_wait(dbscan_server *srv, uint64_t job_id, int64_t timeout_us, double *latency_us);
 /* Waits for every admitted job, stops the worker and frees the slots.  Jobs
- * still queued are dropped. */
+ * still queued are dropped (they complete with DBSCAN_ERR_BUSY).  Threads
+ * blocked in dbscan_serve_wait at that moment return (with their job's status)
+ * before anything is freed; no submit, poll or wait call may start after
+ * destroy has returned, and none may start once it has begun except by a
+ * thread that was already blocked in wait. */
 int dbscan_serve_destroy(dbscan_server *srv);
 
 /* ---- Entry point that allocates nothing (the paper has no counterpart) ----
@@ -292,9 +306,13 @@ int dbscan_serve_destroy(dbscan_server *srv);
  *   labels_out device int32 [n]
  *   stream     cudaStream_t (NULL = legacy default stream); the call waits for it
  * Runs on the calling thread's current device.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress) and caches it, so
- * make that first call before any stream capture.  All calls share the one
- * array: calls whose work overlaps on the GPU race and must not be issued.
+ * looks up the array's device address (cudaGetSymbolAddress) and caches it
+ * with the id of the current CUDA context; a call in a new context on that
+ * device (after cudaDeviceReset, say) looks it up again.  Make the first call,
+ * and the first after such a change, before any stream capture.  All calls
+ * share the one array and it keeps the last call's contents (each call clears
+ * what must start at zero): calls whose work overlaps on the GPU race and must
+ * not be issued.
  * Returns DBSCAN_ERR_NOT_QUANTISED for off-grid input. */
 #define DBSCAN_NOALLOC_MAX_N 16384
 #define DBSCAN_NOALLOC_MAX_D 16

@@ -97,6 +97,14 @@ class Plan:
     def phase_times(self):
         return B.dbscan_plan_phase_times(self.handle)
 
+    def counters(self) -> list[int]:
+        """The plan's device counters after its last run (waits for the plan's stream)."""
+        return B.dbscan_plan_counters(self.handle)
+
+    def pair_tests(self) -> list[int]:
+        """Pair predicates the last run evaluated: [count, merge, border, outer-ring merge] passes."""
+        return self.counters()[16:20]
+
     def sync(self) -> int:
         return B.dbscan_plan_sync(self.handle)
 

@@ -44,7 +44,8 @@ class dbscan_opts(ctypes.Structure):
 class dbscan_stats(ctypes.Structure):
     _fields_ = [("n_clusters", c_i64), ("n_core", c_i64), ("n_border", c_i64), ("n_noise", c_i64),
                 ("candidate_pairs", c_i64), ("band_pairs", c_i64), ("path", c_i32), ("cells", c_i32),
-                ("threshold", c_i64), ("ms_total", c_f32), ("kernels", c_i32), ("reserved_f", c_f32 * 6)]
+                ("threshold", c_i64), ("ms_total", c_f32), ("kernels", c_i32), ("pair_tests", c_i64),
+                ("reserved_f", c_f32 * 4)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
@@ -197,9 +198,12 @@ def dbscan_tc_verify(plan: int, points: int, n: int, d: int, eps: float, bf16: i
     return rep.as_dict()
 
 
+DBSCAN_NCTR = 32  # device counters per plan; 16..19 = pair tests of the count, merge, border, outer-ring passes
+
+
 def dbscan_plan_counters(plan: int) -> list[int]:
-    out = (ctypes.c_uint64 * 16)()
-    _check(lib().dbscan_plan_counters(plan, out, 16), "dbscan_plan_counters")
+    out = (ctypes.c_uint64 * DBSCAN_NCTR)()
+    _check(lib().dbscan_plan_counters(plan, out, DBSCAN_NCTR), "dbscan_plan_counters")
     return list(out)
 
 

@@ -50,7 +50,7 @@ size_t layout(DbWork &w, const dbscan_opts &o, char *base) {
     w.scan_part_cap = n / 2048 + 4;
     w.scan_part = c.take<int32_t>(w.scan_part_cap);
     w.status = c.take<unsigned>(4);
-    w.ctr = c.take<unsigned long long>(16);
+    w.ctr = c.take<unsigned long long>(DB_NCTR);
     const bool grid = o.grid != DBSCAN_GRID_OFF && o.max_d >= 1;
     if (grid) {
         int bits = 10;
@@ -161,7 +161,8 @@ int plan_run(dbscan_plan *plan, const float *points, int64_t n, int32_t d, float
     const bool sync = o.synchronous || stats;
     if (o.synchronous && cudaMemsetAsync(plan->w.status, 0, sizeof(unsigned), st) != cudaSuccess)
         return DBSCAN_ERR_CUDA;
-    if (cudaMemsetAsync(plan->w.ctr, 0, sizeof(unsigned long long) * 16, st) != cudaSuccess) return DBSCAN_ERR_CUDA;
+    if (cudaMemsetAsync(plan->w.ctr, 0, sizeof(unsigned long long) * DB_NCTR, st) != cudaSuccess)
+        return DBSCAN_ERR_CUDA;
     if (stats) cudaEventRecord(plan->ev0, st);
     plan->marks.begin(st);
 
@@ -205,7 +206,7 @@ int plan_run(dbscan_plan *plan, const float *points, int64_t n, int32_t d, float
     if (stats) cudaEventRecord(plan->ev1, st);
     if (!sync) return DBSCAN_OK;
 
-    if (cudaMemcpyAsync(plan->h_ctr, plan->w.ctr, sizeof(unsigned long long) * 16, cudaMemcpyDeviceToHost, st) !=
+    if (cudaMemcpyAsync(plan->h_ctr, plan->w.ctr, sizeof(unsigned long long) * DB_NCTR, cudaMemcpyDeviceToHost, st) !=
         cudaSuccess)
         return DBSCAN_ERR_CUDA;
     const int s = plan_read_status(plan, !o.synchronous);
@@ -218,6 +219,8 @@ int plan_run(dbscan_plan *plan, const float *points, int64_t n, int32_t d, float
         stats->n_clusters = (int64_t)c[5];
         stats->path = path;
         stats->band_pairs = (int64_t)c[6];
+        stats->pair_tests =
+            (int64_t)(c[DB_CTR_EVAL] + c[DB_CTR_EVAL + 1] + c[DB_CTR_EVAL + 2] + c[DB_CTR_EVAL + 3]);
         if (path == DBSCAN_PATH_GRID) {
             stats->candidate_pairs = (int64_t)c[1];
             stats->cells = (int32_t)(c[0] >> 32);
@@ -229,6 +232,87 @@ int plan_run(dbscan_plan *plan, const float *points, int64_t n, int32_t d, float
         stats->ms_total = ms;
         stats->kernels = plan->marks.kernels;
     }
+    return DBSCAN_OK;
+}
+
+int plan_create_unbound(dbscan_plan **out, const dbscan_opts &o) {
+    *out = nullptr;
+    if (o.max_n < 0 || o.max_n > INT32_MAX / 2 || o.max_d < 1 || o.max_d > 64) return DBSCAN_ERR_ARG;
+    if (o.precision < 0 || o.precision > 3 || o.grid < 0 || o.grid > 2 || o.label_mode < 0 || o.label_mode > 1 ||
+        o.profile < 0 || o.profile > 1)
+        return DBSCAN_ERR_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device < 0 || o.device >= ndev) return DBSCAN_ERR_CUDA;
+    DeviceGuard dg(o.device);
+    dbscan_plan *p = new (std::nothrow) dbscan_plan();
+    if (!p) return DBSCAN_ERR_OOM;
+    p->opts = o;
+    p->stream = (cudaStream_t)o.stream;
+    p->w.marks = &p->marks;
+    if (o.profile) {
+        p->marks.on = true;
+        bool ok = cudaEventCreate(&p->marks.start) == cudaSuccess;
+        for (int i = 0; i < PhaseMarks::kMax && ok; ++i) ok = cudaEventCreate(&p->marks.ev[i]) == cudaSuccess;
+        if (!ok) {
+            dbscan_plan_destroy(p);
+            return DBSCAN_ERR_CUDA;
+        }
+    }
+    if (o.grid != DBSCAN_GRID_OFF) {  // grid path: side stream and fork/join events
+        bool ok = cudaStreamCreateWithFlags(&p->w.side, cudaStreamNonBlocking) == cudaSuccess;
+        for (int i = 0; i < 4 && ok; ++i)
+            ok = cudaEventCreateWithFlags(&p->w.fj[i], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            dbscan_plan_destroy(p);
+            return DBSCAN_ERR_CUDA;
+        }
+    }
+    if (cudaMallocHost(&p->h_status, sizeof(unsigned) * 4) != cudaSuccess ||
+        cudaMallocHost(&p->h_ctr, sizeof(unsigned long long) * DB_NCTR) != cudaSuccess ||
+        cudaEventCreate(&p->ev0) != cudaSuccess || cudaEventCreate(&p->ev1) != cudaSuccess) {
+        dbscan_plan_destroy(p);
+        return DBSCAN_ERR_CUDA;
+    }
+    *out = p;
+    return DBSCAN_OK;
+}
+
+// Layout options for instances up to (n, d): with exact_d, d is the only
+// dimension the workspace serves, so the eps-grid's arrays are left out for
+// d > 3 (a plan's max_d is only an upper bound, so plans keep them).
+static dbscan_opts layout_opts(const dbscan_opts &o, int64_t n, int32_t d, bool exact_d) {
+    dbscan_opts q = o;
+    q.max_n = n;
+    q.max_d = d;
+    if (exact_d && d > 3) q.grid = DBSCAN_GRID_OFF;
+    return q;
+}
+
+size_t plan_workspace_bytes_for(const dbscan_opts &o, int64_t n, int32_t d, bool exact_d) {
+    DbWork w{};
+    return layout(w, layout_opts(o, n, d, exact_d), nullptr);
+}
+
+int plan_bind_workspace(dbscan_plan *p, void *base, size_t bytes, int64_t n, int32_t d, bool exact_d) {
+    if (!p || !base || d < 1 || d > 64 || n < 0) return DBSCAN_ERR_ARG;
+    const dbscan_opts q = layout_opts(p->opts, n, d, exact_d);
+    if (plan_workspace_bytes_for(p->opts, n, d, exact_d) > bytes) return DBSCAN_ERR_ARG;
+    PhaseMarks *marks = p->w.marks;
+    cudaStream_t side = p->w.side;
+    cudaEvent_t fj[4] = {p->w.fj[0], p->w.fj[1], p->w.fj[2], p->w.fj[3]};
+    DbWork w{};
+    layout(w, q, static_cast<char *>(base));
+    w.marks = marks;
+    w.side = side;
+    for (int i = 0; i < 4; ++i) w.fj[i] = fj[i];
+    p->w = w;
+    p->opts.max_n = n;
+    p->opts.max_d = d;
+    p->ws_base = base;
+    p->ws_bytes = bytes;
+    DeviceGuard dg(p->opts.device);
+    if (cudaMemsetAsync(p->w.status, 0, sizeof(unsigned), p->stream) != cudaSuccess) return DBSCAN_ERR_CUDA;
+    if (p->owns_ws && cudaStreamSynchronize(p->stream) != cudaSuccess) return DBSCAN_ERR_CUDA;
     return DBSCAN_OK;
 }
 
@@ -253,57 +337,21 @@ int dbscan_plan_create(dbscan_plan **out, const dbscan_opts *opts) {
     dbscan_opts o;
     if (opts) o = *opts;
     else dbscan_opts_default(&o);
-    if (o.max_n < 0 || o.max_n > INT32_MAX / 2 || o.max_d < 1 || o.max_d > 64) return DBSCAN_ERR_ARG;
-    if (o.precision < 0 || o.precision > 3 || o.grid < 0 || o.grid > 2 || o.label_mode < 0 || o.label_mode > 1 ||
-        o.profile < 0 || o.profile > 1)
-        return DBSCAN_ERR_ARG;
-    int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device < 0 || o.device >= ndev) return DBSCAN_ERR_CUDA;
+    dbscan_plan *p = nullptr;
+    int rc = plan_create_unbound(&p, o);
+    if (rc) return rc;
     DeviceGuard dg(o.device);
-    dbscan_plan *p = new (std::nothrow) dbscan_plan();
-    if (!p) return DBSCAN_ERR_OOM;
-    p->opts = o;
-    p->stream = (cudaStream_t)o.stream;
-    DbWork w{};
-    const size_t bytes = layout(w, o, nullptr);
+    const size_t bytes = plan_workspace_bytes_for(o, o.max_n, o.max_d, false);
     void *base = nullptr;
     if (cudaMalloc(&base, bytes) != cudaSuccess) {
         cudaGetLastError();
-        delete p;
+        dbscan_plan_destroy(p);
         return DBSCAN_ERR_OOM;
     }
-    p->ws_base = base;
-    p->ws_bytes = bytes;
-    layout(p->w, o, static_cast<char *>(base));
-    p->w.marks = &p->marks;
-    if (o.profile) {
-        p->marks.on = true;
-        bool ok = cudaEventCreate(&p->marks.start) == cudaSuccess;
-        for (int i = 0; i < PhaseMarks::kMax && ok; ++i) ok = cudaEventCreate(&p->marks.ev[i]) == cudaSuccess;
-        if (!ok) {
-            dbscan_plan_destroy(p);
-            return DBSCAN_ERR_CUDA;
-        }
-    }
-    if (p->w.hcap > 0) {  // grid path: side stream and fork/join events
-        bool ok = cudaStreamCreateWithFlags(&p->w.side, cudaStreamNonBlocking) == cudaSuccess;
-        for (int i = 0; i < 4 && ok; ++i)
-            ok = cudaEventCreateWithFlags(&p->w.fj[i], cudaEventDisableTiming) == cudaSuccess;
-        if (!ok) {
-            dbscan_plan_destroy(p);
-            return DBSCAN_ERR_CUDA;
-        }
-    }
-    if (cudaMallocHost(&p->h_status, sizeof(unsigned) * 4) != cudaSuccess ||
-        cudaMallocHost(&p->h_ctr, sizeof(unsigned long long) * 16) != cudaSuccess ||
-        cudaEventCreate(&p->ev0) != cudaSuccess || cudaEventCreate(&p->ev1) != cudaSuccess) {
+    p->owns_ws = true;
+    if ((rc = plan_bind_workspace(p, base, bytes, o.max_n, o.max_d, false)) != DBSCAN_OK) {
         dbscan_plan_destroy(p);
-        return DBSCAN_ERR_CUDA;
-    }
-    if (cudaMemsetAsync(p->w.status, 0, sizeof(unsigned), p->stream) != cudaSuccess ||
-        cudaStreamSynchronize(p->stream) != cudaSuccess) {
-        dbscan_plan_destroy(p);
-        return DBSCAN_ERR_CUDA;
+        return rc;
     }
     *out = p;
     return DBSCAN_OK;
@@ -314,7 +362,7 @@ int dbscan_plan_destroy(dbscan_plan *p) {
     DeviceGuard dg(p->opts.device);
     cudaStreamSynchronize(p->stream);
     plan_release_extras(p);
-    if (p->ws_base) cudaFree(p->ws_base);
+    if (p->ws_base && p->owns_ws) cudaFree(p->ws_base);
     if (p->h_status) cudaFreeHost(p->h_status);
     if (p->h_ctr) cudaFreeHost(p->h_ctr);
     if (p->ev0) cudaEventDestroy(p->ev0);
@@ -396,10 +444,11 @@ int dbscan_tc_verify(dbscan_plan *plan, const float *points, int64_t n, int32_t 
     if (T >= (1 << 24)) return DBSCAN_ERR_UNSUPPORTED;
     DeviceGuard dg(plan->opts.device);
     cudaStream_t st = plan->stream;
-    if (cudaMemsetAsync(plan->w.ctr, 0, sizeof(unsigned long long) * 16, st) != cudaSuccess) return DBSCAN_ERR_CUDA;
+    if (cudaMemsetAsync(plan->w.ctr, 0, sizeof(unsigned long long) * DB_NCTR, st) != cudaSuccess)
+        return DBSCAN_ERR_CUDA;
     if (cudaMemsetAsync(plan->w.status, 0, sizeof(unsigned), st) != cudaSuccess) return DBSCAN_ERR_CUDA;
     if (launch_tc_verify(plan->w, points, n, d, T, bf16 != 0, st) != cudaSuccess) return DBSCAN_ERR_CUDA;
-    if (cudaMemcpyAsync(plan->h_ctr, plan->w.ctr, sizeof(unsigned long long) * 16, cudaMemcpyDeviceToHost, st) !=
+    if (cudaMemcpyAsync(plan->h_ctr, plan->w.ctr, sizeof(unsigned long long) * DB_NCTR, cudaMemcpyDeviceToHost, st) !=
         cudaSuccess)
         return DBSCAN_ERR_CUDA;
     const int s = plan_read_status(plan, true);
@@ -416,8 +465,8 @@ int dbscan_tc_verify(dbscan_plan *plan, const float *points, int64_t n, int32_t 
 int dbscan_plan_counters(dbscan_plan *plan, uint64_t *out, int32_t n) {
     if (!plan || !out || n < 0) return DBSCAN_ERR_ARG;
     DeviceGuard dg(plan->opts.device);
-    const int k = std::min(n, 16);
-    if (cudaMemcpyAsync(plan->h_ctr, plan->w.ctr, sizeof(unsigned long long) * 16, cudaMemcpyDeviceToHost,
+    const int k = std::min(n, DB_NCTR);
+    if (cudaMemcpyAsync(plan->h_ctr, plan->w.ctr, sizeof(unsigned long long) * DB_NCTR, cudaMemcpyDeviceToHost,
                         plan->stream) != cudaSuccess ||
         cudaStreamSynchronize(plan->stream) != cudaSuccess)
         return DBSCAN_ERR_CUDA;

@@ -35,6 +35,7 @@ struct ApArgs {
     int ntiles;
     int splits;
     int early;  // count pass: stop a row tile once every row has this many (0: exact counts)
+    unsigned long long *ev;  // pair tests evaluated, [0] count, [1] merge, [2] border pass (nullable)
 };
 
 
@@ -105,6 +106,8 @@ __device__ __forceinline__ void ap_tile_body(const ApArgs &a, int rt, int ct_beg
     }
     int bm[4] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX};
     int rootp[4] = {-2, -2, -2, -2};  // union: last known root of each row's set
+    const int rows_in = min(BM, a.n - row0);
+    unsigned long long evaluated = 0;  // pairs of the tiles scored (thread 0's count)
 
     for (int ct = ct_begin; ct < ct_end; ++ct) {
         const int col0 = ct * BN;
@@ -148,6 +151,7 @@ __device__ __forceinline__ void ap_tile_body(const ApArgs &a, int rt, int ct_beg
             __syncthreads();
         }
         if (!want_cols) continue;
+        if (tid == 0) evaluated += (unsigned long long)rows_in * min(BN, a.n - col0);
 
         float acc[4][4];
         int iacc[4][4];
@@ -243,6 +247,7 @@ __device__ __forceinline__ void ap_tile_body(const ApArgs &a, int rt, int ct_beg
         }
     }
 
+    if (tid == 0 && a.ev && evaluated) atomicAdd(a.ev + PASS, evaluated);
     if (PASS == PASS_COUNT) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) {

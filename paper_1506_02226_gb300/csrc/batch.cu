@@ -95,7 +95,7 @@ template <int PASS>
 __global__ void __launch_bounds__(NT) batch_pass_kernel(const BInst *__restrict__ t, const BHdr *__restrict__ hdr,
                                                         int ch_tiles, int *work, const float *P, int *count,
                                                         const uint8_t *core, int *parent, int *border,
-                                                        unsigned *status) {
+                                                        unsigned *status, unsigned long long *ev) {
     __shared__ int item_s;
     const int nitems = hdr->total_items, ninst = hdr->count;
     while (true) {
@@ -125,6 +125,7 @@ __global__ void __launch_bounds__(NT) batch_pass_kernel(const BInst *__restrict_
         a.ntiles = I.ntiles;
         a.splits = 1;
         a.early = I.min_pts;  // batch outputs labels only: counts may stop at min_pts
+        a.ev = ev ? ev + 3 * i : nullptr;  // pair tests evaluated by instance i's three passes
         switch (I.dp) {  // block-uniform: one instance per work item
             case 1: ap_tile_body<1, MODE_GRAM, PASS>(a, rt, ct0, ct1); break;
             case 2: ap_tile_body<2, MODE_GRAM, PASS>(a, rt, ct0, ct1); break;
@@ -213,6 +214,8 @@ struct BatchState {
     int *d_work = nullptr;
     unsigned *d_status = nullptr;
     int *d_istats = nullptr;
+    unsigned long long *d_ev = nullptr;  // pair tests evaluated per instance and pass [count][3]
+    unsigned long long *h_ev = nullptr;
     BInst *h_table = nullptr;
     BHdr *h_hdr = nullptr;
     int *h_istats = nullptr;
@@ -231,6 +234,7 @@ void batch_release(BatchState *b) {
     if (b->h_table) cudaFreeHost(b->h_table);
     if (b->h_hdr) cudaFreeHost(b->h_hdr);
     if (b->h_istats) cudaFreeHost(b->h_istats);
+    if (b->h_ev) cudaFreeHost(b->h_ev);
     if (b->h_status) cudaFreeHost(b->h_status);
     delete b;
 }
@@ -255,7 +259,8 @@ int batch_reserve(BatchState *b, int count, int64_t points, int64_t pfloats) {
     const size_t o_table = take(sizeof(BInst) * nc), o_hdr = take(sizeof(BHdr)), o_pinst = take(4 * np),
                  o_P = take(4 * nf), o_count = take(4 * np), o_core = take(np), o_parent = take(4 * np),
                  o_border = take(4 * np), o_flags = take(4 * np), o_scan = take(4 * (np + 1)),
-                 o_part = take(4 * part), o_work = take(4 * 8), o_status = take(16), o_istats = take(16 * nc);
+                 o_part = take(4 * part), o_work = take(4 * 8), o_status = take(16), o_istats = take(16 * nc),
+                 o_ev = take(24 * (size_t)nc);
     if (b->graph) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
@@ -263,9 +268,11 @@ int batch_reserve(BatchState *b, int count, int64_t points, int64_t pfloats) {
     if (b->dev) cudaFree(b->dev);
     if (b->h_table) cudaFreeHost(b->h_table);
     if (b->h_istats) cudaFreeHost(b->h_istats);
+    if (b->h_ev) cudaFreeHost(b->h_ev);
     b->dev = nullptr;
     b->h_table = nullptr;
     b->h_istats = nullptr;
+    b->h_ev = nullptr;
     if (cudaMalloc(&b->dev, off) != cudaSuccess) {
         cudaGetLastError();
         b->cap_count = 0;
@@ -273,7 +280,8 @@ int batch_reserve(BatchState *b, int count, int64_t points, int64_t pfloats) {
         return DBSCAN_ERR_OOM;
     }
     if (cudaMallocHost(&b->h_table, sizeof(BInst) * nc) != cudaSuccess ||
-        cudaMallocHost(&b->h_istats, 16 * (size_t)nc) != cudaSuccess)
+        cudaMallocHost(&b->h_istats, 16 * (size_t)nc) != cudaSuccess ||
+        cudaMallocHost(&b->h_ev, 24 * (size_t)nc) != cudaSuccess)
         return DBSCAN_ERR_OOM;
     if (!b->h_hdr && cudaMallocHost(&b->h_hdr, sizeof(BHdr)) != cudaSuccess) return DBSCAN_ERR_OOM;
     if (!b->h_status && cudaMallocHost(&b->h_status, 16) != cudaSuccess) return DBSCAN_ERR_OOM;
@@ -294,6 +302,7 @@ int batch_reserve(BatchState *b, int count, int64_t points, int64_t pfloats) {
     b->d_work = reinterpret_cast<int *>(base + o_work);
     b->d_status = reinterpret_cast<unsigned *>(base + o_status);
     b->d_istats = reinterpret_cast<int *>(base + o_istats);
+    b->d_ev = reinterpret_cast<unsigned long long *>(base + o_ev);
     b->cap_count = nc;
     b->cap_points = np;
     b->cap_pfloats = nf;
@@ -349,19 +358,21 @@ cudaError_t enqueue_batch(BatchState *b, int label_mode, bool stats, int ch, int
     if ((e = cudaMemsetAsync(b->d_work, 0, 4 * 8, st))) return e;
     if ((e = cudaMemsetAsync(b->d_count, 0, 4 * (size_t)b->cap_points, st))) return e;
     if (stats && (e = cudaMemsetAsync(b->d_istats, 0, 16 * (size_t)b->cap_count, st))) return e;
+    if (stats && (e = cudaMemsetAsync(b->d_ev, 0, 24 * (size_t)b->cap_count, st))) return e;
     batch_prep_kernel<<<egrid, 256, 0, st>>>(b->d_table, b->d_hdr, b->d_pinst, b->d_P, b->d_status);
     pm->kernel("batch_prep", st);
     batch_pass_kernel<PASS_COUNT><<<pgrid, NT, 0, st>>>(b->d_table, b->d_hdr, ch, b->d_work + 0, b->d_P, b->d_count,
-                                                        b->d_core, b->d_parent, b->d_border, b->d_status);
+                                                        b->d_core, b->d_parent, b->d_border, b->d_status, stats ? b->d_ev : nullptr);
     pm->kernel("batch_count", st);
     batch_core_init_kernel<<<egrid, 256, 0, st>>>(b->d_table, b->d_hdr, b->d_pinst, b->d_count, b->d_core,
                                                   b->d_parent, b->d_border);
     pm->kernel("batch_core_init", st);
     batch_pass_kernel<PASS_UNION><<<pgrid, NT, 0, st>>>(b->d_table, b->d_hdr, ch, b->d_work + 1, b->d_P, b->d_count,
-                                                        b->d_core, b->d_parent, b->d_border, b->d_status);
+                                                        b->d_core, b->d_parent, b->d_border, b->d_status, stats ? b->d_ev : nullptr);
     pm->kernel("batch_union", st);
     batch_pass_kernel<PASS_BORDER><<<pgrid, NT, 0, st>>>(b->d_table, b->d_hdr, ch, b->d_work + 2, b->d_P,
-                                                         b->d_count, b->d_core, b->d_parent, b->d_border, b->d_status);
+                                                         b->d_count, b->d_core, b->d_parent, b->d_border, b->d_status,
+                                                         stats ? b->d_ev : nullptr);
     pm->kernel("batch_border", st);
     batch_label_kernel<<<egrid, 256, 0, st>>>(b->d_table, b->d_hdr, b->d_pinst, b->d_core, b->d_parent, b->d_border,
                                               b->d_flags, stats ? b->d_istats : nullptr);
@@ -375,6 +386,8 @@ cudaError_t enqueue_batch(BatchState *b, int label_mode, bool stats, int ch, int
     }
     if (stats && (e = cudaMemcpyAsync(b->h_istats, b->d_istats, 16 * (size_t)b->cap_count, cudaMemcpyDeviceToHost,
                                       st)))
+        return e;
+    if (stats && (e = cudaMemcpyAsync(b->h_ev, b->d_ev, 24 * (size_t)b->cap_count, cudaMemcpyDeviceToHost, st)))
         return e;
     if ((e = cudaMemcpyAsync(b->h_status, b->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st))) return e;
     if ((e = cudaMemsetAsync(b->d_status, 0, sizeof(unsigned), st))) return e;
@@ -512,6 +525,12 @@ extern "C" int dbscan_batch(dbscan_plan *plan, const dbscan_instance *inst, int3
     if (bits & DB_EBIT_TIMEOUT) return DBSCAN_ERR_TIMEOUT;
     if (bits) return DBSCAN_ERR_CUDA;
     if (stats) {
+        // the batch's pair tests per pass, also left in the plan's counters 16..18
+        unsigned long long tot[4] = {0, 0, 0, 0};
+        for (int i = 0; i < count; ++i)
+            for (int k = 0; k < 3; ++k) tot[k] += b->h_ev[3 * i + k];
+        if (cudaMemcpy(plan->w.ctr + DB_CTR_EVAL, tot, sizeof(tot), cudaMemcpyHostToDevice) != cudaSuccess)
+            return DBSCAN_ERR_CUDA;
         for (int i = 0; i < count; ++i) {
             dbscan_stats &o = per_inst[i];
             std::memset(&o, 0, sizeof(o));
@@ -524,6 +543,7 @@ extern "C" int dbscan_batch(dbscan_plan *plan, const dbscan_instance *inst, int3
             const double e = (double)inst[i].eps;
             o.threshold = (int64_t)std::floor(e * e * 1048576.0);
             o.kernels = 6 + (label_mode == DBSCAN_LABEL_COMPACT ? 4 : 0);
+            o.pair_tests = (int64_t)(b->h_ev[3 * i] + b->h_ev[3 * i + 1] + b->h_ev[3 * i + 2]);
         }
     }
     return DBSCAN_OK;

@@ -186,6 +186,17 @@ __device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile 
     }
 }
 
+// Bounded wait that ignores the abort flag: the abort path uses it to let a
+// role's own copies or MMAs in flight land before the CTA's memory goes away.
+__device__ __noinline__ bool mbar_wait_quiet(uint64_t *bar, uint32_t parity, unsigned long long budget_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    while (globaltimer() - t0 <= budget_ns)
+        if (mbar_try_wait_sleep(bar, parity)) return true;
+    return false;
+}
+constexpr unsigned long long kDrainNs = 100000000ull;  // 100 ms: copies and MMAs land in microseconds
+
 // Packed FP32 pairs (sm_100 and later): two lanes of arithmetic per
 // instruction, each rounded exactly as its scalar counterpart.
 __device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
@@ -315,8 +326,10 @@ struct __align__(16) SmemT {
     uint64_t a_full[2], a_empty[2];
     uint64_t b_full[NS], b_empty[NS];
     uint64_t t_full[2], t_empty[2];
+    uint64_t drain;                  // abort path: one more MMA commit, waited for by the issuer
     uint32_t tmem_base;
     int abort_flag;
+    int drain_failed;                // a role's bounded drain wait gave up
     // union pass: hints of the column points' sets, per accumulator buffer and
     // column half (shared by the four warps of a half; a buffer is refilled only
     // after all eight epilogue warps have released it)
@@ -396,7 +409,9 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
             mbar_init(&S.b_full[i], 1);
             mbar_init(&S.b_empty[i], 1 + EPI_WARPS);
         }
+        mbar_init(&S.drain, 1);
         S.abort_flag = 0;
+        S.drain_failed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -418,6 +433,8 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
         // ---------------- producer ----------------
         if (lane == 0) {
             int t = 0, ia = 0;
+            int last_b[NSTAGE], last_a[2] = {-1, -1};  // phase of each buffer's last copy (-1: none)
+            for (int s = 0; s < NSTAGE; ++s) last_b[s] = -1;
             for (int w = blockIdx.x; w < nitems && !*abort_flag; w += gridDim.x, ++ia) {
                 int rt, c0, c1;
                 item_range(a, w, nR, nC, rt, c0, c1);
@@ -426,17 +443,28 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
                 mbar_arrive_expect_tx(&S.a_full[ab], a_bytes + sizeof(MetaBlock));
                 bulk_g2s(S.A[ab], a.opR + (size_t)rt * TM * KS, a_bytes, &S.a_full[ab]);
                 bulk_g2s(&S.metaA[ab], a.metaR + rt, sizeof(MetaBlock), &S.a_full[ab]);
+                last_a[ab] = ia >> 1;
                 for (int ct = c0; ct < c1; ++ct, ++t) {
                     const int s = t % NSTAGE;
                     if (!TC_WAIT(w_prod, mbar_wait(&S.b_empty[s], ((t / NSTAGE) & 1) ^ 1, abort_flag, a.wait_ns))) break;
                     mbar_arrive_expect_tx(&S.b_full[s], b_bytes + 2 * sizeof(MetaBlock));
                     bulk_g2s(S.B[s], a.opC + (size_t)ct * TN * KS, b_bytes, &S.b_full[s]);
                     bulk_g2s(&S.metaB[s][0], a.metaC + 2 * ct, 2 * sizeof(MetaBlock), &S.b_full[s]);
+                    last_b[s] = t / NSTAGE;
                 }
             }
-            // Drain: every copy issued has landed once its stage's "empty" barrier
-            // completes again (the consumers arrive after the copy completed), or
-            // after a final bounded wait on the "full" barriers below.
+            // On a clean finish every copy has been consumed, so it has landed.
+            // After an abort, wait (bounded) until the last copy into each buffer
+            // has landed: a buffer holds at most one copy in flight, so the
+            // parity of its last phase identifies it.
+            if (*abort_flag) {
+                bool ok = true;
+                for (int s = 0; s < NSTAGE; ++s)
+                    if (last_b[s] >= 0) ok &= mbar_wait_quiet(&S.b_full[s], last_b[s] & 1, kDrainNs);
+                for (int ab = 0; ab < 2; ++ab)
+                    if (last_a[ab] >= 0) ok &= mbar_wait_quiet(&S.a_full[ab], last_a[ab] & 1, kDrainNs);
+                if (!ok) S.drain_failed = 1;
+            }
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
@@ -446,6 +474,7 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
             const uint32_t idesc = idesc_f16(BF16);
             int t = 0, ia = 0;
             bool clean = true;
+            unsigned long long evaluated = 0;  // pairs of the tiles multiplied
             for (int w = blockIdx.x; w < nitems && !*abort_flag; w += gridDim.x, ++ia) {
                 int rt, c0, c1;
                 item_range(a, w, nR, nC, rt, c0, c1);
@@ -478,6 +507,7 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
                     }
                     mma_commit(&S.t_full[b]);   // accumulator ready for the epilogue
                     mma_commit(&S.b_empty[s]);  // operands of this stage consumed
+                    evaluated += (unsigned long long)min(TM, nR - rt * TM) * min(TN, nC - ct * TN);
                 }
                 mma_commit(&S.a_empty[ab]);
                 if (!ok) {
@@ -497,6 +527,13 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
                     const int il = ab + ((ia - 1 - ab) / 2) * 2;
                     mbar_wait(&S.a_empty[ab], (il >> 1) & 1, abort_flag, a.wait_ns);
                 }
+            }
+            if (a.pass != TC_VERIFY && evaluated) atomicAdd(a.ctr + DB_CTR_EVAL + a.pass, evaluated);
+            // After an abort: one more commit, which arrives once every MMA this
+            // thread issued has completed, and a bounded wait for it.
+            if (*abort_flag && t > 0) {
+                mma_commit(&S.drain);
+                if (!mbar_wait_quiet(&S.drain, 0, kDrainNs)) S.drain_failed = 1;
             }
         }
     } else {
@@ -768,9 +805,11 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
     __syncthreads();
     if (S.abort_flag) {
         if (threadIdx.x == 0) atomicOr(a.status, DB_EBIT_TIMEOUT);
-        // Let in-flight copies and MMAs land before the CTA's memory goes away:
-        // wait (bounded) for every barrier to be quiescent.
-        if (threadIdx.x == 0) {
+        // The producer has waited (bounded) for the last copy into each buffer
+        // and the MMA issuer for a final commit that follows all its MMAs, so
+        // nothing of this CTA is in flight.  Only if one of those waits gave up
+        // does thread 0 also spin 20 ms before the tensor memory is freed.
+        if (threadIdx.x == 0 && S.drain_failed) {
             const uint64_t t0 = globaltimer();
             while (globaltimer() - t0 < 20000000ull) {
             }

@@ -321,6 +321,7 @@ struct PairArgs {
     const unsigned *cell_key;
     const int *nbr;   // neighbour cell lists, row stride g.noff
     const int *ncnt;  // (adjacent count << 16) | count
+    unsigned long long *ev;  // pair tests evaluated: [0] count, [1] merge, [2] border, [3] outer-ring merge
 };
 
 // Count pass (Section IV-B, fused pair test + count).  Per cell A:
@@ -343,6 +344,11 @@ __global__ void __launch_bounds__(256, 6) grid_count_kernel(PairArgs a, int min_
     const int ncells = (int)(*a.ctr0 >> 32);
     const int lim = exact ? INT_MAX : min_pts;
     const int noff = a.g.noff;
+    // pair tests of each warp, kept in shared memory (no register held across the loops)
+    __shared__ unsigned wev[8];
+    unsigned &ev = wev[threadIdx.x >> 5];
+    if (lane == 0) ev = 0;
+    __syncwarp();
     for (int A = warp; A < ncells; A += nwarps) {
         const int sA = a.cell_start[A], cA = a.cell_count[A];
         const int *row = a.nbr + (size_t)A * noff;
@@ -374,6 +380,7 @@ __global__ void __launch_bounds__(256, 6) grid_count_kernel(PairArgs a, int min_
                     const int B = row[k];
                     const int s = a.cell_start[B], e = s + a.cell_count[B];
                     for (int q = s; q < e; ++q) cnt += is_nbr<D>(cp, px2, py2, pz2, a.spts[q]);
+                    if (lane == 0) ev += (unsigned)(min(32, cA - i0) * (e - s));  // the lanes holding a point
                 }
                 if (v) {
                     const bool core = cnt >= min_pts;
@@ -404,6 +411,7 @@ __global__ void __launch_bounds__(256, 6) grid_count_kernel(PairArgs a, int min_
                         const int q = locate(j, incl, c, s);
                         qq[u] = j < total ? a.spts[q] : make_float4(0.f, 0.f, 0.f, -1e30f);
                     }
+                    if (lane == 0) ev += (unsigned)(__popc(pend) * min(128, total - base));
                     for (unsigned m = pend; m; m &= m - 1) {
                         const int i = __ffs(m) - 1;
                         const float cp = __shfl_sync(FULL, cpm, i), px2 = __shfl_sync(FULL, px2m, i);
@@ -471,6 +479,8 @@ __global__ void __launch_bounds__(256, 6) grid_count_kernel(PairArgs a, int min_
             if (lane == 0) cell_mid[A] = a.spts[sA + (int)(near & 0xffffffffull)];
         }
     }
+    __syncwarp();
+    db::block_sum_add(a.ev + 0, lane == 0 ? ev : 0u);
 }
 
 // Merge pass (Section IV-C).  The core points of one cell are already one set
@@ -494,6 +504,7 @@ __global__ void __launch_bounds__(256) grid_union_kernel(PairArgs a, const uint8
     const int ncells = (int)(*a.ctr0 >> 32);
     float4 *yb = ybuf[wib];
     uint8_t *yc = ycore[wib];
+    unsigned ev = 0;  // pair tests this lane accounts for (a warp sees far below 2^32 per launch)
     for (int A = warp; A < ncells; A += nwarps) {
         const int repA = a.cell_rep[A];
         if (repA == DB_NONE) continue;
@@ -517,6 +528,7 @@ __global__ void __launch_bounds__(256) grid_union_kernel(PairArgs a, const uint8
             if (need) need = db::uf_find(parent, repA) != db::uf_find(parent, repB);
             // the two central core points first: a hit unites at once, lanes in parallel
             const bool hit = need && use_mid && is_nbr<D>(cmA, mx2, my2, mz2, mB);
+            ev += need && use_mid;
             if (hit) db::uf_unite(parent, repA, repB, status);
             need = need && !hit;
             unsigned todo = __ballot_sync(FULL, need);
@@ -550,11 +562,13 @@ __global__ void __launch_bounds__(256) grid_union_kernel(PairArgs a, const uint8
                     for (int x0 = 0; x0 < cX && !found; x0 += 32) {
                         const int xi = x0 + lane;
                         const bool vx = xi < cX && score[sX + xi];
-                        if (!__any_sync(FULL, vx)) continue;
+                        const unsigned vxm = __ballot_sync(FULL, vx);
+                        if (!vxm) continue;
                         const float4 px = a.spts[sX + (xi < cX ? xi : 0)];
                         const float cp = a.g.Tp1 + px.w, px2 = 2.f * px.x, py2 = 2.f * px.y, pz2 = 2.f * px.z;
                         for (int k = 0; k < ny; ++k) {
                             if (!yc[k]) continue;
+                            if (lane == 0) ev += (unsigned)__popc(vxm);
                             if (__any_sync(FULL, vx && is_nbr<D>(cp, px2, py2, pz2, yb[k]))) {
                                 found = true;
                                 break;
@@ -567,6 +581,7 @@ __global__ void __launch_bounds__(256) grid_union_kernel(PairArgs a, const uint8
             }
         }
     }
+    db::block_sum_add(a.ev + (far_ring ? 3 : 1), ev);  // the outer ring has a counter of its own
 }
 
 // Border pass: each non-core point takes its smallest-index core neighbour
@@ -583,6 +598,7 @@ __global__ void __launch_bounds__(256) grid_border_kernel(PairArgs a, int min_pt
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
     const int ncells = (int)(*a.ctr0 >> 32);
     const int noff = a.g.noff;
+    unsigned ev = 0;  // pair tests this lane accounts for (a warp sees far below 2^32 per launch)
     for (int A = warp; A < ncells; A += nwarps) {
         const int sA = a.cell_start[A], cA = a.cell_count[A];
         if (cA >= min_pts) continue;  // all core
@@ -627,8 +643,11 @@ __global__ void __launch_bounds__(256) grid_border_kernel(PairArgs a, int min_pt
                         const int bk = __shfl_sync(FULL, b, k);
                         int best = bk;
 #pragma unroll
-                        for (int u = 0; u < 4; ++u)
-                            if (qi[u] < best && is_nbr<D>(cp, px2, py2, pz2, qq[u])) best = qi[u];
+                        for (int u = 0; u < 4; ++u) {
+                            const bool better = qi[u] < best;  // else the pair needs no test
+                            ev += better;
+                            if (better && is_nbr<D>(cp, px2, py2, pz2, qq[u])) best = qi[u];
+                        }
                         best = (int)__reduce_min_sync(FULL, (unsigned)best);
                         if (lane == k) b = best;
                     }
@@ -637,6 +656,7 @@ __global__ void __launch_bounds__(256) grid_border_kernel(PairArgs a, int min_pt
             if (mine) bord[sA + i] = b;
         }
     }
+    db::block_sum_add(a.ev + 2, ev);
 }
 
 // Root of every cell with cores, once per cell (a thread per cell), and the
@@ -760,7 +780,7 @@ template <int D>
 cudaError_t grid_pair_passes(const DbWork &w, const GridGeom &g, int n, int min_pts, bool exact, int32_t *labels,
                              int32_t *counts_out, uint8_t *core_out, cudaStream_t st) {
     PairArgs a{g,          w.ctr,      w.spts,     w.sidx, w.cell_start, w.cell_count,
-               w.cell_rep, w.cell_mid, w.cell_key, w.nbr,  w.ncnt};
+               w.cell_rep, w.cell_mid, w.cell_key, w.nbr,  w.ncnt,       w.ctr + DB_CTR_EVAL};
     const int wgrid = 152 * 16;  // 8 warps per block, warps stride over the cells
     grid_count_kernel<D><<<wgrid, 256, 0, st>>>(a, min_pts, exact ? 1 : 0, w.score, w.cell_rep, w.cell_mid,
                                                 w.parent, counts_out, core_out);

@@ -16,6 +16,14 @@
 #define DB_EBIT_OVERFLOW 4u    // a device-side list ran out of room
 
 #define DB_NONE 0x7fffffff     // "no index" (larger than every point index)
+
+// Device counters of a run (DbWork::ctr, DB_NCTR 64-bit slots):
+//   0 grid cells|points, 1 grid candidate pairs, 2..5 core/border/noise/clusters,
+//   6 band pairs rechecked, 7..8 band verification, 9..13 pipeline diagnostics,
+//   16..19 pair tests evaluated by the count, merge, border and (grid path)
+//   outer-ring merge passes.
+#define DB_NCTR 32
+#define DB_CTR_EVAL 16
 #define DB_HASH_EMPTY 0xffffffffu
 
 namespace db {
@@ -95,6 +103,21 @@ __device__ __forceinline__ bool on_grid(float x, int &u) {
     return ok;
 }
 
+// Sum of v over the block added to *dst by one global atomic.  Every thread
+// of the block must call it (it synchronises the block).
+__device__ __forceinline__ void block_sum_add(unsigned long long *dst, unsigned long long v) {
+    __shared__ unsigned long long part[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) t += part[w];
+        if (t) atomicAdd(dst, t);
+    }
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -146,7 +169,7 @@ struct DbWork {
     int32_t *scan_part;     // scan partials
     int64_t scan_part_cap;
     unsigned *status;       // device error bits
-    unsigned long long *ctr;  // counters: [0]=cells|points, [1]=candidate pairs, [2..5]=stats, [6]=band pairs
+    unsigned long long *ctr;  // DB_NCTR counters (slots listed beside DB_NCTR)
     // grid path
     int64_t hcap;           // hash slots (power of two >= 2 cap_n)
     int32_t hbits;

@@ -14,11 +14,13 @@
 // The array's name, used in host code, is a host-side stand-in, not a device
 // address.  So the first call on a device (with that device current) asks the
 // runtime for the real address with cudaGetSymbolAddress, checks the result
-// and caches it for that device.  That first call should therefore come before
-// any stream capture.  All calls share the one array and it keeps the last
-// call's contents: everything that must start at zero is cleared on the
-// stream at the start of each call, and two calls whose work overlaps on the
-// GPU race on the array.  No cudaMalloc, cudaFree or allocating library routine
+// and caches it for that device, keyed by the id of the current CUDA context:
+// if the context changes (cudaDeviceReset, a new primary context), the next
+// call looks the address up again.  The first call on a device, and the first
+// after such a change, should therefore come before any stream capture.  All
+// calls share the one array and it keeps the last call's contents: everything
+// that must start at zero is cleared on the stream at the start of each call,
+// and two calls whose work overlaps on the GPU race on the array.  No cudaMalloc, cudaFree or allocating library routine
 // is called.
 #include <algorithm>
 #include <cmath>
@@ -46,23 +48,60 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-unsigned char *g_scratch_addr[kMaxDevices] = {};
+struct ScratchEntry {
+    unsigned char *addr = nullptr;
+    unsigned long long ctx_id = 0;  // context the address belongs to (0: unknown)
+};
+ScratchEntry g_entry[kMaxDevices];
 
-// Device address of g_scratch on the calling thread's current device.
+// Unique id of the calling thread's current CUDA context (0 if there is none
+// or the driver does not say).  The driver's entry points are looked up through
+// the runtime, so the library needs no link to the driver library.
+unsigned long long current_context_id() {
+    using GetCurrent = int (*)(void **);
+    using GetId = int (*)(void *, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+        cudaGetLastError();
+    });
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&ctx) == 0 && ctx && get_id(ctx, &id) == 0) return id;
+    return 0;
+}
+
+// Device address of g_scratch in the calling thread's current device and
+// context.  Looked up once per device and cached with the context's id; a new
+// context on that device (after cudaDeviceReset, say) triggers a new lookup.
 int scratch_address(unsigned char **out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DBSCAN_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
+    ScratchEntry &e = g_entry[dev];
+    const unsigned long long ctx = current_context_id();
+    if (!e.addr || (ctx != 0 && ctx != e.ctx_id)) {
         void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess || !p) {
+        const cudaError_t err = cudaGetSymbolAddress(&p, g_scratch);
+        if (err != cudaSuccess || !p) {
             cudaGetLastError();
+            e.addr = nullptr;
             return DBSCAN_ERR_CUDA;
         }
-        g_scratch_addr[dev] = static_cast<unsigned char *>(p);
+        e.addr = static_cast<unsigned char *>(p);
+        e.ctx_id = current_context_id();  // the lookup may have created the context
     }
-    *out = g_scratch_addr[dev];
+    *out = e.addr;
     return DBSCAN_OK;
 }
 

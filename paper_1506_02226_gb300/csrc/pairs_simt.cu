@@ -139,6 +139,7 @@ cudaError_t launch_allpairs_simt(const DbWork &w, int64_t n64, int32_t d, int32_
     a.status = w.status;
     a.ntiles = (n + BM - 1) / BM;
     a.early = exact_counts ? 0 : min_pts;
+    a.ev = w.ctr + DB_CTR_EVAL;
     // Enough blocks to fill 152 SMs a few times over, splitting the column range.
     int splits = (4 * 152 + a.ntiles - 1) / a.ntiles;
     a.splits = std::max(1, std::min(splits, a.ntiles));

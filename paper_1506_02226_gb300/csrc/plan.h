@@ -10,6 +10,7 @@ struct dbscan_plan {
     cudaStream_t stream = nullptr;
     void *ws_base = nullptr;  // one device allocation, carved into DbWork
     size_t ws_bytes = 0;
+    bool owns_ws = false;     // false: the workspace was bound by its owner (a server slot)
     DbWork w{};
     unsigned *h_status = nullptr;          // pinned
     unsigned long long *h_ctr = nullptr;   // pinned
@@ -26,6 +27,15 @@ struct dbscan_plan {
 int plan_run(dbscan_plan *plan, const float *points, int64_t n, int32_t d, float eps, int32_t min_pts,
              int32_t *labels, int32_t *counts_out, uint8_t *core_out, dbscan_stats *stats);
 int plan_read_status(dbscan_plan *plan, bool clear);
+// A plan with streams, events and host buffers but no device workspace yet.
+int plan_create_unbound(dbscan_plan **out, const dbscan_opts &o);
+// Device bytes of the workspace for instances up to (n, d) under o's options
+// (exact_d: instances of exactly this d, so no eps-grid arrays when d > 3).
+size_t plan_workspace_bytes_for(const dbscan_opts &o, int64_t n, int32_t d, bool exact_d);
+// Carves [base, base + bytes) into the plan's workspace for instances up to
+// (n, d) (exact_d as above); the plan then accepts such instances.  The memory
+// stays the caller's unless the plan owns it (owns_ws).
+int plan_bind_workspace(dbscan_plan *p, void *base, size_t bytes, int64_t n, int32_t d, bool exact_d);
 int plan_ensure_staging(dbscan_plan *plan, int64_t n, int32_t d);
 void plan_release_extras(dbscan_plan *plan);
 void batch_release(BatchState *b);

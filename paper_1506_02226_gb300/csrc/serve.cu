@@ -51,7 +51,8 @@ struct dbscan_server {
     dbscan_serve_opts opts{};
     std::vector<Slot> slots;
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
+    std::condition_variable cv_work, cv_done, cv_idle;
+    int waiters = 0;  // threads inside dbscan_serve_wait (destroy frees nothing while any is)
     std::deque<Job *> queue;
     std::unordered_map<uint64_t, Job *> jobs;
     uint64_t next_id = 1;
@@ -229,8 +230,12 @@ int dbscan_serve_wait(dbscan_server *s, uint64_t job_id, int64_t timeout_us, dou
     if (it == s->jobs.end()) return DBSCAN_ERR_NOT_FOUND;
     Job *j = it->second;
     auto ready = [j] { return j->done; };
+    ++s->waiters;
+    bool ok = true;
     if (timeout_us < 0) s->cv_done.wait(lk, ready);
-    else if (!s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready)) return DBSCAN_ERR_TIMEOUT;
+    else ok = s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready);
+    if (--s->waiters == 0 && s->stop) s->cv_idle.notify_all();
+    if (!ok) return DBSCAN_ERR_TIMEOUT;
     if (latency_us)
         *latency_us = std::chrono::duration<double, std::micro>(j->t_done - j->t_submit).count();
     const int st = j->status;
@@ -251,8 +256,14 @@ int dbscan_serve_destroy(dbscan_server *s) {
         s->queue.clear();
     }
     s->cv_work.notify_all();
-    if (s->worker.joinable()) s->worker.join();
-    s->cv_done.notify_all();
+    if (s->worker.joinable()) s->worker.join();  // every admitted job is done now
+    {
+        // Wake the threads blocked in dbscan_serve_wait (all their jobs are done)
+        // and free nothing until the last has left.
+        std::unique_lock<std::mutex> lk(s->mu);
+        s->cv_done.notify_all();
+        s->cv_idle.wait(lk, [s] { return s->waiters == 0; });
+    }
     for (Slot &sl : s->slots) {
         if (sl.plan) dbscan_plan_destroy(sl.plan);
         if (sl.done_ev) cudaEventDestroy(sl.done_ev);

@@ -48,7 +48,7 @@ def test_binding_covers_the_header(libpath):
 
 
 def test_host_only_calls(libpath):
-    assert binding.dbscan_abi_version() == 1
+    assert binding.dbscan_abi_version() == 2
     assert binding.dbscan_strerror(binding.DBSCAN_ERR_NOT_QUANTISED).startswith("a coordinate")
     assert binding.dbscan_strerror(12345) == "unknown status"
     o = binding.dbscan_opts_default()
@@ -62,6 +62,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(binding.dbscan_stats) == 96
     assert ctypes.sizeof(binding.dbscan_instance) == 40
     assert binding.dbscan_instance.labels_out.offset == 32
+    assert binding.dbscan_stats.pair_tests.offset == 72
 
 
 def test_header_is_plain_c(tmp_path):
@@ -76,6 +77,7 @@ def test_header_is_plain_c(tmp_path):
         "_Static_assert(sizeof(dbscan_opts) == 72, \"opts\");\n"
         "_Static_assert(sizeof(dbscan_stats) == 96, \"stats\");\n"
         "_Static_assert(sizeof(dbscan_instance) == 40, \"instance\");\n"
+        "_Static_assert(offsetof(dbscan_stats, pair_tests) == 72, \"stats.pair_tests\");\n"
         "int use(dbscan_plan *p, const float *x, int32_t *l) {\n"
         "    dbscan_opts o; dbscan_opts_default(&o);\n"
         "    return dbscan_run(p, x, 0, 2, 0.1f, 5, l, (dbscan_stats *)0);\n"

@@ -4,14 +4,17 @@ Some callers cannot call cudaMalloc, for example a service that reserved all
 device memory for its own pool, or code that must not take the allocator's
 locks.  dbscan_run_noalloc takes its scratch from a fixed array inside the
 library instead of a plan.  These tests call it through the C ABI twice in a
-row and check each result against dbscan_run's on the same input; labels are
-integers from an exact predicate, so they must be equal.  This file is
-collected last, so that a run stopping at the first failure has run every
-other test first.
+row and check each result against dbscan_run's on the same input and against
+the oracle; labels are integers from an exact predicate, so they must be equal.
+The calls run largest first (one at the array's size limit), so each later
+call runs over scratch a larger call left behind.  This file is collected
+last, so that a run stopping at the first failure has run every other test
+first.
 """
 import numpy as np
 import pytest
 
+import oracle
 from paper_1506_02226_gb300 import binding as B
 from paper_1506_02226_gb300 import inputs
 
@@ -43,15 +46,19 @@ def _random_instance(seed, n, d):
 
 def test_noalloc_matches_dbscan_run_two_calls_in_a_row():
     small = inputs.small_2d()
-    cases = [
-        (torch.from_numpy(small.points).cuda(), small.eps, small.min_pts, B.DBSCAN_LABEL_ROOT_INDEX),
-        (torch.from_numpy(_random_instance(3, 9000, 16)).cuda(), 0.09, 6, B.DBSCAN_LABEL_COMPACT),
+    cases = [  # largest first: later calls run over what a larger call left in the shared scratch
+        (_random_instance(7, B.DBSCAN_NOALLOC_MAX_N, B.DBSCAN_NOALLOC_MAX_D), 0.08, 8, B.DBSCAN_LABEL_ROOT_INDEX),
+        (_random_instance(3, 9000, 16), 0.09, 6, B.DBSCAN_LABEL_COMPACT),
+        (small.points, small.eps, small.min_pts, B.DBSCAN_LABEL_ROOT_INDEX),
+        (small.points, small.eps, small.min_pts, B.DBSCAN_LABEL_COMPACT),
     ]
-    for x, eps, mp, mode in cases:  # back to back: the shared scratch holds the previous call's data
+    for pts, eps, mp, mode in cases:  # back to back: the shared scratch holds the previous call's data
+        x = torch.from_numpy(pts).cuda()
         got = _noalloc(x, eps, mp, mode)
         want = _with_plan(x, eps, mp, mode)
         np.testing.assert_array_equal(got, want)
-        assert (got >= 0).any()
+        np.testing.assert_array_equal(got, oracle.dbscan(pts, eps, mp, label_mode=mode)[0])
+        assert (got >= 0).any() and (got == -1).any()
 
 
 def test_noalloc_limits_and_errors():
