@@ -47,9 +47,15 @@ WORKLOADS = {
               "Gram pair test", inputs.high_d),
     "highd_bf16": ("200k points, d=64, as highd with BF16 tensor-core Gram pair test", inputs.high_d),
     "highd_simt": ("200k points, d=64, as highd with the exact CUDA-core pair test", inputs.high_d),
+    "midd4": ("200k points, d=4, 50 blobs + 20% noise, eps=0.005*sqrt(d/2), min_pts=10, projected grid",
+              lambda: inputs.mid_d(4)),
+    "midd8": ("200k points, d=8, 50 blobs + 20% noise, eps=0.005*sqrt(d/2), min_pts=10, projected grid",
+              lambda: inputs.mid_d(8)),
 }
 CPU_SAMPLE = {"lowd2": 200_000, "lowd3": 200_000, "small": 2000, "highd": 40_000, "highd_bf16": 40_000,
-              "highd_simt": 40_000}
+              "highd_simt": 40_000, "midd4": 100_000, "midd8": 100_000}
+# workloads whose record also times the same instance on the all-pairs path
+COMPARE_ALLPAIRS = {"midd4", "midd8"}
 PRECISION = {"highd_bf16": 3, "highd_simt": 1}
 
 
@@ -244,8 +250,8 @@ def fp32_peak_tops():
 
 
 def pair_ops(d: int) -> int:
-    """FP32-pipe instructions of one pair test: Gram form d+2 (d <= 8), direct form 2d+1."""
-    return d + 2 if d <= 8 else 2 * d + 1
+    """FP32-pipe instructions of one pair test: Gram form d+2 (d <= 16), direct form 2d+1."""
+    return d + 2 if d <= 16 else 2 * d + 1
 
 
 # ------------------------------------------------------------------ replicas
@@ -268,7 +274,8 @@ def whole_job_rate(units_per_rank: float, world: int, ms_per_step: float) -> flo
 # Device counters 16..19 of a plan: pair tests of the count, merge, border and
 # outer-ring merge passes; the kernels that evaluate pairs, by pass.
 PASS_OF = {"grid_count": 0, "grid_union_near": 1, "grid_border": 2, "grid_union_far": 3,
-           "ap_count": 0, "ap_union": 1, "ap_border": 2, "tc_count": 0, "tc_union": 1, "tc_border": 2}
+           "ap_count": 0, "ap_union": 1, "ap_border": 2, "tc_count": 0, "tc_union": 1, "tc_border": 2,
+           "mid_count": 0, "mid_union": 1, "mid_border": 2}
 
 
 def run_reference(args, wl_name):
@@ -361,7 +368,7 @@ def roofline(dom: str, avg_ms: float, ev: list, n: int, d: int, gs, wl_name: str
             roof["epilogue_fp32"] = {"ops_per_pair": 3, "achieved": alu, "peak": fp32_peak, "unit": "T ops/s",
                                      "frac": alu / fp32_peak}
             return roof
-        ops_pp = pair_ops(d) if not dom.startswith("grid_") else d + 2
+        ops_pp = pair_ops(d) if not dom.startswith(("grid_", "mid_")) else d + 2
         fp32_peak, sms = fp32_peak_tops()
         ach = pairs * ops_pp / sec / 1e12
         alu = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "T FP32-pipe ops/s",
@@ -502,6 +509,26 @@ def run_ours(args, wl_name, baseline=True, steps=None):
     e2e_ms = 1e3 * statistics.mean(e2e_s)
     eplan.close()
     plan.close()
+    allpairs = None
+    if wl_name in COMPARE_ALLPAIRS:  # the same instance with the grid off (the paper's all-pairs test)
+        aplan = Plan(max_n=n, max_d=d, synchronous=False, stream=stream, grid=B.DBSCAN_GRID_OFF, precision=prec)
+        a_ms = []
+        with torch.cuda.stream(stream):
+            for r in range(2 + 3):
+                flush.fill_(1)
+                ev0.record(stream)
+                aplan.run(x, inst.eps, inst.min_pts, labels=labels)
+                ev1.record(stream)
+                ev1.synchronize()
+                if r >= 2:
+                    a_ms.append(ev0.elapsed_time(ev1))
+        if aplan.sync() != 0:
+            raise RuntimeError("all-pairs comparison run reported an error")
+        a_pairs = sum(aplan.pair_tests())
+        aplan.close()
+        allpairs = {"ms_per_step": statistics.mean(a_ms), "pair_tests_per_step": a_pairs,
+                    "speedup_of_grid": statistics.mean(a_ms) / ms_per_step,
+                    "what": "the same instance on the all-pairs CUDA-core path (grid off), 3 steps"}
 
     if rank != 0:
         return None
@@ -522,13 +549,15 @@ def run_ours(args, wl_name, baseline=True, steps=None):
         "scaling": "weak", "vs_baseline": None, "dtype": {2: "f32", 3: "f16" if prec != 3 else "bf16"}.get(
             st0["path"], "f32"), "data": "synthetic",
         "config": {"workload": wl_name + ": " + desc, "n": n, "d": d, "eps": inst.eps, "min_pts": inst.min_pts,
-                   "path": {1: "eps-grid", 2: "all-pairs SIMT", 3: "all-pairs tensor-core"}.get(st0["path"]),
+                   "path": {1: "eps-grid", 2: "all-pairs SIMT", 3: "all-pairs tensor-core",
+                            4: "projected grid"}.get(st0["path"]),
                    "l2": "flushed by a 256 MiB write before every timed step", "parallelism": f"replicas x{world}"},
         "pair_tests_per_step": pairs_per_step,
         "pair_tests_by_pass": dict(zip(["count", "merge", "border", "merge_outer_ring"], ev_pass)),
         "pair_tests_note": "pair predicates the device evaluated (its per-pass counters), averaged over the "
                            "timed steps; pairs decided without a test are not counted",
-        "candidate_pairs_per_step": candidates if st0["path"] == B.DBSCAN_PATH_GRID else n * n,
+        "candidate_pairs_per_step": (candidates if st0["path"] in (B.DBSCAN_PATH_GRID, B.DBSCAN_PATH_GRID_PROJECTED)
+                                     else n * n),
         "evaluated_vs_min": pairs_per_step / max(n * (n - 1) / 2, 1),
         "band_pairs_per_step": st0["band_pairs"],
         "points_per_s": world * n / (ms_per_step * 1e-3),
@@ -537,6 +566,7 @@ def run_ours(args, wl_name, baseline=True, steps=None):
         "kernels_ms_note": "each kernel alone (a profiled run, kernels serialised, L2 flushed before each run)",
         "roofline": roof,
         "roofline_next": others,
+        "allpairs": allpairs,
         "cpu_baseline": cpu,
         "e2e": {"value": pairs_per_step / (e2e_ms * 1e-3) / 1e9, "unit": "G pair-tests/s", "ms_per_step": e2e_ms,
                 "points_per_s": n / (e2e_ms * 1e-3), "h2d_bytes_per_step": 4 * n * d, "d2h_bytes_per_step": 4 * n},
@@ -793,11 +823,59 @@ def run_serve(args):
     }
 
 
+def run_paper_compare(args, n=23_040, steps=3):
+    """The paper's materialised pipeline (dbscan_run_paper: distance matrix,
+    primitive-cluster matrix, one merge launch per target) against this
+    library's fused all-pairs and eps-grid runs on the same 3-D input."""
+    from paper_1506_02226_gb300 import build as cuda_build
+    cuda_build.build()
+    import torch
+    from paper_1506_02226_gb300 import binding as B
+    from paper_1506_02226_gb300.api import Plan
+    inst = inputs.paper_3d(n)
+    x = torch.from_numpy(inst.points).cuda()
+    lab = torch.empty(n, dtype=torch.int32, device="cuda")
+    out = {"workload": f"paper3d: {n} points, d=3, 50 blobs + 20% noise, eps=0.02, min_pts=10 (synthetic stand-in "
+                       "for the paper's unnamed 3-D set at its N)", "n": n}
+    with Plan(max_n=n, max_d=3, profile=True) as p:
+        phases, total = {}, []
+        for r in range(1 + steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, st = p.run_paper(x, inst.eps, inst.min_pts, labels=lab, stats=True)
+            wall = time.perf_counter() - t0
+            if r >= 1:
+                total.append(wall * 1e3)
+                for nm, ms in p.phase_times():
+                    phases.setdefault(nm, []).append(ms)
+        want = lab.cpu().numpy().copy()
+        out["paper_pipeline"] = {"ms_per_run": statistics.mean(total), "merge_sweeps": st["cells"],
+                                 "phases_ms": {k: statistics.mean(v) for k, v in phases.items()},
+                                 "what": "Section IV as the paper builds it: N x N distance matrix, primitive-cluster "
+                                         "matrix and valid vector, one merge launch per valid target per sweep "
+                                         "(host-driven, wall clock)"}
+    for name, grid in (("fused_allpairs", B.DBSCAN_GRID_OFF), ("grid", B.DBSCAN_GRID_AUTO)):
+        with Plan(max_n=n, max_d=3, grid=grid, profile=True) as p:
+            ts = []
+            for r in range(3 + steps):
+                _, st = p.run(x, inst.eps, inst.min_pts, labels=lab, stats=True)
+                if r >= 3:
+                    ts.append(st["ms_total"])
+            got = lab.cpu().numpy()
+            if not np.array_equal(got, want):
+                raise RuntimeError(f"paper pipeline and {name} labels differ")
+            out[name] = {"ms_per_run": statistics.mean(ts), "phases_ms": dict(p.phase_times())}
+    out["speedup_fused_over_paper"] = out["paper_pipeline"]["ms_per_run"] / out["fused_allpairs"]["ms_per_run"]
+    out["speedup_grid_over_paper"] = out["paper_pipeline"]["ms_per_run"] / out["grid"]["ms_per_run"]
+    out["labels_identical"] = True
+    return out
+
+
 def compact(rec: dict) -> dict:
     """The figures of a workload's record that the default line carries."""
     keep = ("metric", "value", "unit", "ms_per_step", "dtype", "pair_tests_per_step", "candidate_pairs_per_step",
             "evaluated_vs_min", "band_pairs_per_step", "points_per_s", "launch_loop", "closed_loop", "poisson",
-            "server_memory", "config", "clocks")
+            "server_memory", "allpairs", "config", "clocks")
     out = {k: rec[k] for k in keep if k in rec}
     r = rec.get("roofline")
     if r:
@@ -818,7 +896,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch", "serve"], default=None,
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch", "serve", "paper"], default=None,
                     help="print the full record of one workload (default: lowd2 with the others as subrecords)")
     ap.add_argument("--no-subrecords", action="store_true", help="default run without the other workloads")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU baseline (for profiler runs)")
@@ -846,6 +924,9 @@ def main():
     if wl == "serve":
         print(json.dumps(run_serve(args)))
         return
+    if wl == "paper":
+        print(json.dumps(run_paper_compare(args)))
+        return
     if wl is not None:
         rec = run_ours(args, wl)
         if rec is not None:
@@ -858,8 +939,10 @@ def main():
         sub["lowd3"] = compact(run_ours(args, "lowd3", baseline=False))
         sub["highd_fp16"] = compact(run_ours(args, "highd", steps=min(args.steps, 10)))
         sub["highd_bf16"] = compact(run_ours(args, "highd_bf16", baseline=False, steps=min(args.steps, 10)))
+        sub["midd8"] = compact(run_ours(args, "midd8", baseline=False, steps=min(args.steps, 10)))
         sub["batch"] = compact(run_batch(args, steps=min(args.steps, 10)))
         sub["serve"] = compact(run_serve(args))
+        sub["paper_pipeline"] = run_paper_compare(args)
         rec["subrecords"] = sub
     if rec is not None:
         print(json.dumps(rec))

@@ -70,8 +70,9 @@ extern "C" {
 #define DBSCAN_PREC_BF16_GRAM 3  /* tcgen05 BF16 Gram product (two-term split) + exact recheck of the band */
 
 /* Candidate generation. */
-#define DBSCAN_GRID_AUTO 0 /* eps-grid for d <= 3, all pairs otherwise */
-#define DBSCAN_GRID_ON 1   /* eps-grid (d <= 3 only; else DBSCAN_ERR_UNSUPPORTED) */
+#define DBSCAN_GRID_AUTO 0 /* eps-grid for d <= 3, projected grid for 4 <= d <= 8 (when its cells, of side
+                              floor(sqrt(T)) + 1 units, split each axis at least 4 ways), all pairs otherwise */
+#define DBSCAN_GRID_ON 1   /* a grid path (d <= 8 and, for d >= 4, cells as above; else DBSCAN_ERR_UNSUPPORTED) */
 #define DBSCAN_GRID_OFF 2  /* all pairs */
 
 /* Label numbering. */
@@ -83,6 +84,8 @@ extern "C" {
 #define DBSCAN_PATH_GRID 1
 #define DBSCAN_PATH_ALLPAIRS_SIMT 2
 #define DBSCAN_PATH_ALLPAIRS_TC 3
+#define DBSCAN_PATH_GRID_PROJECTED 4 /* 4 <= d <= 8: cells of the first three coordinates, full-d test */
+#define DBSCAN_PATH_PAPER 5          /* dbscan_run_paper: the paper's materialised matrices */
 
 typedef struct dbscan_plan dbscan_plan;
 
@@ -108,7 +111,7 @@ typedef struct dbscan_stats {
     int64_t n_border;        /* border points */
     int64_t n_noise;         /* noise points */
     int64_t candidate_pairs; /* ordered pairs the method must decide: n^2 (all pairs) or the pairs
-                                inside each cell's eps-grid neighbourhood (grid path) */
+                                inside each cell's neighbourhood (grid paths) */
     int64_t band_pairs;      /* tensor-core path: pairs inside the rounding band, rechecked exactly */
     int32_t path;            /* DBSCAN_PATH_* */
     int32_t cells;           /* grid path: occupied cells */
@@ -160,6 +163,22 @@ int dbscan_run_detail(dbscan_plan *plan, const float *points, int64_t n, int32_t
  * end-to-end call. */
 int dbscan_run_host(dbscan_plan *plan, const float *host_points, int64_t n, int32_t d, float eps,
                     int32_t min_pts, int32_t *host_labels, dbscan_stats *stats);
+
+/* The paper's own pipeline, as a comparison variant (Section IV): an N x N
+ * matrix of squared distances (Section IV-A), the primitive-cluster matrix and
+ * the `valid` vector of core points (Section IV-B), and one merge launch per
+ * target cluster, ORing every mergeable cluster's row into the target's
+ * (Section IV-C), swept over the targets until a sweep merges nothing.  Two
+ * clusters merge iff a core point lies in both rows.  Labels are those of
+ * dbscan_run (same canonical form and label mode).  Arguments as dbscan_run,
+ * with d <= 16 and n <= DBSCAN_PAPER_MAX_N (the matrices take 5 n^2 bytes of
+ * device memory, allocated by the plan on first use and kept until it is
+ * destroyed).  Always synchronous (the merge sweeps are driven from the host);
+ * stats->cells receives the number of sweeps.  DBSCAN_ERR_OOM if the matrices
+ * do not fit. */
+#define DBSCAN_PAPER_MAX_N 65536
+int dbscan_run_paper(dbscan_plan *plan, const float *points, int64_t n, int32_t d, float eps, int32_t min_pts,
+                     int32_t *labels_out, dbscan_stats *stats);
 
 /* Waits for everything enqueued on the plan and returns the first device-side
  * error recorded since the last sync (then clears it). */
@@ -250,24 +269,44 @@ typedef struct dbscan_server dbscan_server;
 typedef struct dbscan_serve_opts {
     int32_t device;
     int32_t slots;            /* jobs that may be on the device at once (each slot: one stream, one plan) */
-    int64_t hbm_budget_bytes; /* admission cap on the summed workspace of the jobs on the device */
+    int64_t hbm_budget_bytes; /* admission cap on the summed device workspace of the jobs on the device */
     int32_t label_mode;       /* DBSCAN_LABEL_* */
     int32_t precision;        /* DBSCAN_PREC_* */
-    int64_t max_n;            /* largest job accepted (slot plans are sized for it) */
+    int64_t max_n;            /* largest job accepted */
     int32_t max_d;            /* largest d accepted */
     int32_t max_queue;        /* jobs waiting for a slot before submit answers DBSCAN_ERR_BUSY */
     int32_t reserved[4];
 } dbscan_serve_opts;
 
+/* What a server has done and holds (dbscan_serve_info). */
+typedef struct dbscan_serve_stats {
+    int64_t jobs_done;                /* jobs completed since the server started */
+    int64_t jobs_queued;              /* jobs waiting for admission now */
+    int32_t jobs_running;             /* jobs on the device now */
+    int32_t max_jobs_running;         /* most jobs that were on the device at once */
+    int64_t hbm_budget_bytes;         /* the admission cap */
+    int64_t bytes_in_flight;          /* summed workspace of the jobs on the device now */
+    int64_t peak_bytes_in_flight;     /* largest such sum so far */
+    int64_t pool_reserved_bytes;      /* device memory the server's pool holds now */
+    int64_t pool_peak_reserved_bytes; /* largest it has held */
+    int64_t reserved[4];
+} dbscan_serve_stats;
+
 /* Defaults: device 0, 8 slots, 120 GiB budget, root-index labels, PREC_AUTO,
  * max_n 500,000, max_d 64, max_queue 1,000,000. */
 void dbscan_serve_opts_default(dbscan_serve_opts *opts);
 
-/* Starts a server: allocates every slot's plan and starts the worker thread
- * that admits queued jobs to free slots (continuous batching: a job is
- * admitted as soon as a slot and enough of the HBM budget are free, while
- * other jobs still run), enqueues them on the slot's stream and completes them
- * when their events fire. */
+/* Starts a server: creates every slot (stream, event, a plan without
+ * workspace), a stream-ordered device memory pool and the worker thread that
+ * admits queued jobs to free slots (continuous batching: a job is admitted as
+ * soon as a slot and enough of the HBM budget are free, while other jobs still
+ * run).  An admitted job's workspace, exactly what its (n, d) needs
+ * (dbscan_serve_job_bytes), is taken from the pool on its slot's stream and
+ * returned to it there behind the job's kernels, so the budget limits the
+ * device memory the jobs on the device hold; a job larger than the whole
+ * budget still runs, alone.  Freed blocks stay in the pool (up to the budget)
+ * for later jobs.  The serving form of the paper's method has no counterpart
+ * in the paper: it is the continuous-batching server this library adds. */
 int dbscan_serve_create(dbscan_server **out, const dbscan_serve_opts *opts);
 /* Queues a job (Section I's three steps on one instance, as dbscan_run).  The
  * instance's device buffers must stay valid until it is done.  *job_id
@@ -283,6 +322,14 @@ int dbscan_serve_poll(dbscan_server *srv, uint64_t job_id, int32_t *done);
  * (nullable) receives its submit-to-done time in microseconds.  Returns the
  * job's status.  Thread-safe. */
 int dbscan_serve_wait(dbscan_server *srv, uint64_t job_id, int64_t timeout_us, double *latency_us);
+/* Statistics of the server (host, filled): jobs, concurrency, budget, the
+ * workspace bytes of the jobs on the device and what the pool holds.
+ * Thread-safe. */
+int dbscan_serve_info(dbscan_server *srv, dbscan_serve_stats *out);
+/* Device workspace bytes a job of n points in d dimensions holds while it
+ * runs (what admission charges against the budget); -1 for n or d out of the
+ * server's range. */
+int64_t dbscan_serve_job_bytes(const dbscan_server *srv, int64_t n, int32_t d);
 /* Waits for every admitted job, stops the worker and frees the slots.  Jobs
  * still queued are dropped (they complete with DBSCAN_ERR_BUSY).  Threads
  * blocked in dbscan_serve_wait at that moment return (with their job's status)

@@ -82,6 +82,19 @@ class Plan:
             raise B.DbscanError(rc, "dbscan_run_detail")
         return labels, counts, core, st.as_dict()
 
+    def run_paper(self, points: torch.Tensor, eps: float, min_pts: int, labels: torch.Tensor | None = None,
+                  stats: bool = False):
+        """The paper's materialised pipeline (comparison variant); same labels as run()."""
+        self._check_points(points)
+        n, d = points.shape
+        if labels is None:
+            labels = torch.empty(n, dtype=torch.int32, device=points.device)
+        st = B.dbscan_stats() if stats else None
+        rc = B.dbscan_run_paper(self.handle, points.data_ptr(), n, d, eps, min_pts, labels.data_ptr(), st)
+        if rc:
+            raise B.DbscanError(rc, "dbscan_run_paper")
+        return (labels, st.as_dict()) if stats else labels
+
     def run_host(self, points: torch.Tensor, eps: float, min_pts: int, labels: torch.Tensor | None = None):
         """End-to-end call on host tensors (pinned for speed): copies in, clusters, copies out."""
         if points.is_cuda or points.dtype != torch.float32 or not points.is_contiguous():

@@ -30,6 +30,8 @@ DBSCAN_PREC_AUTO, DBSCAN_PREC_EXACT_SIMT, DBSCAN_PREC_FP16_GRAM, DBSCAN_PREC_BF1
 DBSCAN_GRID_AUTO, DBSCAN_GRID_ON, DBSCAN_GRID_OFF = 0, 1, 2
 DBSCAN_LABEL_ROOT_INDEX, DBSCAN_LABEL_COMPACT = 0, 1
 DBSCAN_PATH_NONE, DBSCAN_PATH_GRID, DBSCAN_PATH_ALLPAIRS_SIMT, DBSCAN_PATH_ALLPAIRS_TC = 0, 1, 2, 3
+DBSCAN_PATH_GRID_PROJECTED, DBSCAN_PATH_PAPER = 4, 5
+DBSCAN_PAPER_MAX_N = 65536
 DBSCAN_HOOK_NONE, DBSCAN_HOOK_TC_STALL = 0, 1
 
 c_i32, c_i64, c_f32, c_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_void_p
@@ -70,6 +72,15 @@ class dbscan_serve_opts(ctypes.Structure):
                 ("reserved", c_i32 * 4)]
 
 
+class dbscan_serve_stats(ctypes.Structure):
+    _fields_ = [("jobs_done", c_i64), ("jobs_queued", c_i64), ("jobs_running", c_i32), ("max_jobs_running", c_i32),
+                ("hbm_budget_bytes", c_i64), ("bytes_in_flight", c_i64), ("peak_bytes_in_flight", c_i64),
+                ("pool_reserved_bytes", c_i64), ("pool_peak_reserved_bytes", c_i64), ("reserved", c_i64 * 4)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 _SIGS = {
     "dbscan_opts_default": (None, [c_p]),
     "dbscan_plan_create": (ctypes.c_int, [c_p, c_p]),
@@ -77,6 +88,7 @@ _SIGS = {
     "dbscan_run": (ctypes.c_int, [c_p, c_p, c_i64, c_i32, c_f32, c_i32, c_p, c_p]),
     "dbscan_run_detail": (ctypes.c_int, [c_p, c_p, c_i64, c_i32, c_f32, c_i32, c_p, c_p, c_p, c_p]),
     "dbscan_run_host": (ctypes.c_int, [c_p, c_p, c_i64, c_i32, c_f32, c_i32, c_p, c_p]),
+    "dbscan_run_paper": (ctypes.c_int, [c_p, c_p, c_i64, c_i32, c_f32, c_i32, c_p, c_p]),
     "dbscan_plan_sync": (ctypes.c_int, [c_p]),
     "dbscan_plan_workspace_bytes": (c_i64, [c_p]),
     "dbscan_plan_test_hook": (ctypes.c_int, [c_p, c_i32]),
@@ -91,6 +103,8 @@ _SIGS = {
     "dbscan_serve_poll": (ctypes.c_int, [c_p, ctypes.c_uint64, c_p]),
     "dbscan_serve_wait": (ctypes.c_int, [c_p, ctypes.c_uint64, c_i64, c_p]),
     "dbscan_serve_destroy": (ctypes.c_int, [c_p]),
+    "dbscan_serve_info": (ctypes.c_int, [c_p, c_p]),
+    "dbscan_serve_job_bytes": (c_i64, [c_p, c_i64, c_i32]),
     "dbscan_run_noalloc": (ctypes.c_int, [c_p, c_i64, c_i32, c_f32, c_i32, c_i32, c_p, c_p]),
     "dbscan_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "dbscan_abi_version": (c_i32, []),
@@ -170,6 +184,12 @@ def dbscan_run_detail(plan: int, points: int, n: int, d: int, eps: float, min_pt
                       counts_out: int | None, core_out: int | None, stats: dbscan_stats | None = None) -> int:
     return lib().dbscan_run_detail(plan, points, n, d, eps, min_pts, labels_out, counts_out, core_out,
                                    ctypes.byref(stats) if stats is not None else None)
+
+
+def dbscan_run_paper(plan: int, points: int, n: int, d: int, eps: float, min_pts: int, labels_out: int,
+                     stats: dbscan_stats | None = None) -> int:
+    return lib().dbscan_run_paper(plan, points, n, d, eps, min_pts, labels_out,
+                                  ctypes.byref(stats) if stats is not None else None)
 
 
 def dbscan_run_host(plan: int, host_points: int, n: int, d: int, eps: float, min_pts: int, host_labels: int,
@@ -270,3 +290,13 @@ def dbscan_serve_wait(server: int, job_id: int, timeout_us: int = -1) -> tuple[i
 
 def dbscan_serve_destroy(server: int) -> None:
     _check(lib().dbscan_serve_destroy(server), "dbscan_serve_destroy")
+
+
+def dbscan_serve_info(server: int) -> dict:
+    out = dbscan_serve_stats()
+    _check(lib().dbscan_serve_info(server, ctypes.byref(out)), "dbscan_serve_info")
+    return out.as_dict()
+
+
+def dbscan_serve_job_bytes(server: int, n: int, d: int) -> int:
+    return int(lib().dbscan_serve_job_bytes(server, n, d))

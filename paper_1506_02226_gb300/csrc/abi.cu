@@ -103,12 +103,16 @@ size_t layout(DbWork &w, const dbscan_opts &o, char *base) {
     return align_up(c.off, 256);
 }
 
-int status_from_bits(unsigned bits) {
+}  // namespace
+
+int plan_status_from_bits(unsigned bits) {
     if (bits & DB_EBIT_NOT_QUANTISED) return DBSCAN_ERR_NOT_QUANTISED;
     if (bits & DB_EBIT_TIMEOUT) return DBSCAN_ERR_TIMEOUT;
     if (bits & DB_EBIT_OVERFLOW) return DBSCAN_ERR_CUDA;
     return DBSCAN_OK;
 }
+
+namespace {
 
 struct DeviceGuard {
     int prev = -1;
@@ -133,7 +137,7 @@ int plan_read_status(dbscan_plan *plan, bool clear) {
     const unsigned bits = *plan->h_status;
     if (clear && bits && cudaMemsetAsync(plan->w.status, 0, sizeof(unsigned), st) != cudaSuccess)
         return DBSCAN_ERR_CUDA;
-    return status_from_bits(bits);
+    return plan_status_from_bits(bits);
 }
 
 int plan_run(dbscan_plan *plan, const float *points, int64_t n, int32_t d, float eps, int32_t min_pts,
@@ -151,7 +155,7 @@ int plan_run(dbscan_plan *plan, const float *points, int64_t n, int32_t d, float
     // Index ranges counted in int32: the eps-grid's hash (at least 2n slots)
     // and the all-pairs work items (row tiles x column chunks).
     constexpr int64_t kGridMaxN = int64_t(1) << 29, kAllPairsMaxN = int64_t(1) << 25;
-    const bool grid_path = d <= 3 && o.grid != DBSCAN_GRID_OFF && plan->w.hcap > 0;
+    const bool grid_path = d <= 8 && o.grid != DBSCAN_GRID_OFF && plan->w.hcap > 0;
     if (grid_path ? n > kGridMaxN : n > kAllPairsMaxN) return DBSCAN_ERR_UNSUPPORTED;
     const int64_t Dmax = (int64_t)d * 1023 * 1023;
     const int64_t Tc = std::min(T, Dmax);  // same predicate: no pair is farther than Dmax
@@ -171,11 +175,19 @@ int plan_run(dbscan_plan *plan, const float *points, int64_t n, int32_t d, float
     GridGeom g;
     cudaError_t err;
     const bool want_grid = d <= 3 && o.grid != DBSCAN_GRID_OFF && plan->w.hcap > 0;
-    if (o.grid == DBSCAN_GRID_ON && !(d <= 3 && plan->w.hcap > 0)) return DBSCAN_ERR_UNSUPPORTED;
+    // the projected grid (4 <= d <= 8) needs the eps-grid's arrays and row stride >= 8 (4 for d = 4)
+    const bool want_mid = d >= 4 && d <= 8 && o.grid != DBSCAN_GRID_OFF && plan->w.hcap > 0 &&
+                          plan->w.dp_cap >= (d <= 4 ? 4 : 8);
+    if (o.grid == DBSCAN_GRID_ON && !(want_grid || want_mid)) return DBSCAN_ERR_UNSUPPORTED;
     if (want_grid && grid_geometry(d, Tc, n, &g)) {
         path = DBSCAN_PATH_GRID;
         err = launch_grid_path(plan->w, g, points, n, min_pts, exact, labels, counts_out, core_out, st);
+    } else if (want_mid && mid_geometry(d, Tc, n, &g)) {
+        path = DBSCAN_PATH_GRID_PROJECTED;
+        err = launch_mid_grid_path(plan->w, g, points, n, d, min_pts, exact, labels, counts_out, core_out, st);
     } else {
+        if (o.grid == DBSCAN_GRID_ON) return DBSCAN_ERR_UNSUPPORTED;  // eps too large for the cells to prune
+        if (n > kAllPairsMaxN) return DBSCAN_ERR_UNSUPPORTED;
         const bool tc_ok = plan->w.tc_cap_pad > 0 && d <= 64 && Tc < (1 << 24);
         const bool want_tc = o.precision == DBSCAN_PREC_FP16_GRAM || o.precision == DBSCAN_PREC_BF16_GRAM ||
                              (o.precision == DBSCAN_PREC_AUTO && d >= 16 && n >= 4096);
@@ -198,7 +210,8 @@ int plan_run(dbscan_plan *plan, const float *points, int64_t n, int32_t d, float
         if (!err) err = launch_labels_allpairs(plan->w, n, labels, counts_out, core_out, st);
     }
     if (!err && o.label_mode == DBSCAN_LABEL_COMPACT) err = launch_compact(plan->w, n, labels, st);
-    if (!err && stats && path == DBSCAN_PATH_GRID) err = launch_grid_candidates(plan->w, g, n, st);
+    if (!err && stats && (path == DBSCAN_PATH_GRID || path == DBSCAN_PATH_GRID_PROJECTED))
+        err = launch_grid_candidates(plan->w, g, n, path == DBSCAN_PATH_GRID_PROJECTED, st);
     if (err != cudaSuccess) {
         std::fprintf(stderr, "dbscan: launch failed: %s\n", cudaGetErrorString(err));
         return DBSCAN_ERR_CUDA;
@@ -221,7 +234,7 @@ int plan_run(dbscan_plan *plan, const float *points, int64_t n, int32_t d, float
         stats->band_pairs = (int64_t)c[6];
         stats->pair_tests =
             (int64_t)(c[DB_CTR_EVAL] + c[DB_CTR_EVAL + 1] + c[DB_CTR_EVAL + 2] + c[DB_CTR_EVAL + 3]);
-        if (path == DBSCAN_PATH_GRID) {
+        if (path == DBSCAN_PATH_GRID || path == DBSCAN_PATH_GRID_PROJECTED) {
             stats->candidate_pairs = (int64_t)c[1];
             stats->cells = (int32_t)(c[0] >> 32);
         } else {
@@ -278,13 +291,13 @@ int plan_create_unbound(dbscan_plan **out, const dbscan_opts &o) {
 }
 
 // Layout options for instances up to (n, d): with exact_d, d is the only
-// dimension the workspace serves, so the eps-grid's arrays are left out for
-// d > 3 (a plan's max_d is only an upper bound, so plans keep them).
+// dimension the workspace serves, so the grid arrays are left out for d > 8
+// (a plan's max_d is only an upper bound, so plans keep them).
 static dbscan_opts layout_opts(const dbscan_opts &o, int64_t n, int32_t d, bool exact_d) {
     dbscan_opts q = o;
     q.max_n = n;
     q.max_d = d;
-    if (exact_d && d > 3) q.grid = DBSCAN_GRID_OFF;
+    if (exact_d && d > 8) q.grid = DBSCAN_GRID_OFF;
     return q;
 }
 

@@ -3,10 +3,15 @@
 //
 // The score of a pair is T + 1 - D(p,q), an integer, and q is a neighbour
 // iff score >= 1; __saturatef(score) is then exactly 0 or 1.
-//   MODE_GRAM   (d <= 8): score = (T+1 - |p|^2) - |q|^2 + sum_k (2u_pk) u_qk in
-//               FP32.  Every partial sum is an integer of magnitude below
-//               2*d*1023^2 <= 16,744,464 < 2^24, so FP32 holds it exactly.
-//   MODE_DIRECT (FP32, d <= 16, or T + 1 <= 2^24): score = (T+1) - sum (u_pk-u_qk)^2.
+// Rows hold centred units v = u - 512 in [-512, 511] (D is unchanged).
+//   MODE_GRAM   (d <= 16): score = (T+1 - |p|^2) - |q|^2 + sum_k (2v_pk) v_qk
+//               in FP32 (Section IV-B's hoisted form).  After k terms the
+//               partial sum lies in [T+1 - sum_i (|v_pi| + |v_qi|)^2, T+1] (the
+//               terms not yet added are sums of squares, and each one added is
+//               at least -(|v_pi| + |v_qi|)^2 + v_pi^2 + v_qi^2), and
+//               (|v_pi| + |v_qi|)^2 <= 1023^2, so every partial sum is an
+//               integer of magnitude below 16 * 1023^2 < 2^24: FP32 is exact.
+//   MODE_DIRECT (FP32, T + 1 <= 2^24): score = (T+1) - sum (v_pk-v_qk)^2.
 //               Partial sums only decrease; they are exact while >= -2^24, and
 //               once below that they stay below 1, so the decision is exact.
 //   MODE_INT    otherwise: the same in int32.

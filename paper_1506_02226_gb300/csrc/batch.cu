@@ -83,7 +83,7 @@ __global__ void batch_prep_kernel(const BInst *__restrict__ t, const BHdr *__res
             if (k < I.d) {
                 int u;
                 bad |= !db::on_grid(I.x[(size_t)loc * I.d + k], u);
-                v = (float)u;
+                v = (float)(u - 512);  // centred units: the Gram form is exact up to d = 16
             }
             row[k] = v;
         }
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(NT) batch_pass_kernel(const BInst *__restrict_
             case 3: ap_tile_body<3, MODE_GRAM, PASS>(a, rt, ct0, ct1); break;
             case 4: ap_tile_body<4, MODE_GRAM, PASS>(a, rt, ct0, ct1); break;
             case 8: ap_tile_body<8, MODE_GRAM, PASS>(a, rt, ct0, ct1); break;
-            default: ap_tile_body<16, MODE_DIRECT, PASS>(a, rt, ct0, ct1); break;
+            default: ap_tile_body<16, MODE_GRAM, PASS>(a, rt, ct0, ct1); break;
         }
     }
 }
@@ -324,7 +324,7 @@ int64_t build_table(const dbscan_instance *inst, int count, int ch, BInst *t, in
         I.n = (int)in.n;
         I.d = in.d;
         I.dp = dp_for(in.d);  // 1, 2, 3, 4, 8 or 16
-        I.mode = I.dp == 16 ? MODE_DIRECT : MODE_GRAM;
+        I.mode = MODE_GRAM;
         I.Tc = (int)Tc;
         I.Tp1 = (float)(Tc + 1);
         I.min_pts = in.min_pts;

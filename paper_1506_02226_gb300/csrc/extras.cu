@@ -28,4 +28,7 @@ void plan_release_extras(dbscan_plan *p) {
     p->stage_out = nullptr;
     if (p->batch) batch_release(p->batch);
     p->batch = nullptr;
+    if (p->pp_buf) cudaFree(p->pp_buf);
+    p->pp_buf = nullptr;
+    p->pp_bytes = 0;
 }

@@ -53,12 +53,7 @@ __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p) {
     return v;
 }
 
-// Cell hash slot: four consecutive keys (four cells in a row along x) share
-// one 32-byte bucket of the packed table, so the lookups of a cell's
-// x-neighbours, made by neighbouring lanes, touch few sectors.
-__device__ __forceinline__ unsigned hash_slot(unsigned key, int bits) {
-    return ((((key >> 2) * 2654435761u) >> (34 - bits)) << 2) | (key & 3u);
-}
+using db::hash_slot;
 
 __device__ __forceinline__ unsigned cell_key_of(const int *u, const GridGeom &g) {
     unsigned cx = (unsigned)(u[0] / g.c);
@@ -84,9 +79,9 @@ __global__ void grid_prep_kernel(const float *__restrict__ x, int n, GridGeom g,
         if (!ok) atomicOr(status, DB_EBIT_NOT_QUANTISED);
         const unsigned key = cell_key_of(u, g);
         const unsigned mask = (1u << g.hbits) - 1u;
-        unsigned h = hash_slot(key, g.hbits);
-        bool placed = false;
-        for (unsigned probe = 0; probe <= mask; ++probe) {
+        unsigned h = g.dense ? key : hash_slot(key, g.hbits);
+        bool placed = g.dense != 0;  // a dense table needs no probe
+        for (unsigned probe = 0; probe <= mask && !placed; ++probe) {
             unsigned cur = ld_relaxed_u32(hkey + h);
             if (cur == key) { placed = true; break; }
             if (cur == DB_HASH_EMPTY) {
@@ -111,7 +106,7 @@ __global__ void grid_prep_kernel(const float *__restrict__ x, int n, GridGeom g,
 
 constexpr int CELLS_PER_THREAD = 4;
 
-__global__ void grid_cells_kernel(int H, const unsigned *__restrict__ hkey, const int *__restrict__ hcount,
+__global__ void grid_cells_kernel(int H, int dense, const unsigned *__restrict__ hkey, const int *__restrict__ hcount,
                                   int2 *__restrict__ hpack, int *__restrict__ hcursor, int *__restrict__ cell_start,
                                   int *__restrict__ cell_count, unsigned *__restrict__ cell_key,
                                   int *__restrict__ cell_rep, unsigned *__restrict__ occ,
@@ -150,7 +145,7 @@ __global__ void grid_cells_kernel(int H, const unsigned *__restrict__ hkey, cons
     for (int k = 0; k < CELLS_PER_THREAD; ++k) {
         const int s = s0 + k;
         if (cnt[k] > 0) {
-            const unsigned key = hkey[s];
+            const unsigned key = dense ? (unsigned)s : hkey[s];
             cell_start[cid] = start;
             cell_count[cid] = cnt[k];
             cell_key[cid] = key;
@@ -234,13 +229,17 @@ __global__ void grid_nbr_kernel(GridGeom g, const unsigned long long *ctr0, cons
         unsigned h[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            h[u] = hash_slot(k2[u], g.hbits);
+            h[u] = g.dense ? k2[u] : hash_slot(k2[u], g.hbits);
             e[u] = in[u] ? hpack[h[u]] : make_int2((int)DB_HASH_EMPTY, -1);
         }
         int res[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             res[u] = -1;
+            if (g.dense) {  // the slot of a key is the key: found or empty, no probe
+                if ((unsigned)e[u].x == k2[u]) res[u] = e[u].y;
+                continue;
+            }
             // continue probing past other keys (rare at load factor <= 1/2)
             for (unsigned probe = 0; probe <= mask; ++probe) {
                 if ((unsigned)e[u].x == k2[u]) { res[u] = e[u].y; break; }
@@ -730,14 +729,14 @@ __global__ void grid_label_kernel(int n, const int *__restrict__ sidx, const int
 }
 
 __global__ void grid_candidates_kernel(GridGeom g, const unsigned long long *ctr0, const int *__restrict__ cell_count,
-                                       const int *__restrict__ nbr, const int *__restrict__ ncnt,
+                                       const int *__restrict__ nbr, const int *__restrict__ ncnt, int own_listed,
                                        unsigned long long *out) {
     __shared__ unsigned long long red[32];
     const int ncells = (int)(*ctr0 >> 32);
     unsigned long long s = 0;
     for (int A = blockIdx.x * blockDim.x + threadIdx.x; A < ncells; A += gridDim.x * blockDim.x) {
         const long long ca = cell_count[A];
-        long long t = ca;
+        long long t = own_listed ? 0 : ca;
         const int nn = ncnt[A] & 0xffff;
         for (int k = 0; k < nn; ++k) t += cell_count[nbr[(size_t)A * g.noff + k]];
         s += (unsigned long long)(ca * t);
@@ -831,6 +830,7 @@ bool grid_geometry(int32_t d, int64_t Tc, int64_t n, GridGeom *g) {
     int bits = 10;
     while ((int64_t(1) << bits) < 2 * n) ++bits;
     g->hbits = bits;
+    g->dense = 0;  // the launch may switch to a direct table
     int k = 0;
     const int rz = d > 2 ? (int)r : 0, ry = d > 1 ? (int)r : 0, rx = (int)r;
     for (int oz = -rz; oz <= rz; ++oz)
@@ -858,31 +858,32 @@ bool grid_geometry(int32_t d, int64_t Tc, int64_t n, GridGeom *g) {
     return true;
 }
 
-cudaError_t launch_grid_path(const DbWork &w, const GridGeom &g, const float *x, int64_t n64, int32_t min_pts,
+cudaError_t launch_grid_path(const DbWork &w, const GridGeom &g0, const float *x, int64_t n64, int32_t min_pts,
                              bool exact, int32_t *labels, int32_t *counts_out, uint8_t *core_out, cudaStream_t st) {
     const int n = (int)n64;
-    const int64_t H = int64_t(1) << g.hbits;
-    if (H > w.hcap || g.noff > w.noff_cap) return cudaErrorInvalidValue;
-    cudaError_t e;
-    if ((e = cudaMemsetAsync(w.hkey, 0xff, sizeof(unsigned) * H, st))) return e;
-    if ((e = cudaMemsetAsync(w.hcount, 0, sizeof(int) * H, st))) return e;
-    // occupancy bitmap of all G^d cells, when it fits its buffer
+    if ((int64_t(1) << g0.hbits) > w.hcap || g0.noff > w.noff_cap) return cudaErrorInvalidValue;
+    // When all G^d cells fit the table, a cell's slot is its key: no hashing,
+    // and the cells pass scans G^d slots instead of 2^hbits (2-D: 65,536 cells
+    // at eps = 0.005 against 2^20 slots for 500,000 points).
     int64_t all_cells = 1;
-    for (int k = 0; k < g.d; ++k) all_cells *= g.G;
+    for (int k = 0; k < g0.d; ++k) all_cells *= g0.G;
+    GridGeom g = g0;
+    g.dense = all_cells <= w.hcap ? 1 : 0;
+    const int64_t H = g.dense ? all_cells : (int64_t(1) << g.hbits);
+    cudaError_t e;
+    if (!g.dense && (e = cudaMemsetAsync(w.hkey, 0xff, sizeof(unsigned) * H, st))) return e;
+    if ((e = cudaMemsetAsync(w.hcount, 0, sizeof(int) * H, st))) return e;
+    // occupancy bitmap of all G^d cells for the hashed table, when it fits its buffer
     const int64_t occ_words = (all_cells + 31) / 32;
-    unsigned *occ = occ_words <= w.occ_cap ? w.occ : nullptr;
+    unsigned *occ = (!g.dense && occ_words <= w.occ_cap) ? w.occ : nullptr;
     if (occ && (e = cudaMemsetAsync(occ, 0, sizeof(unsigned) * occ_words, st))) return e;
     const int nb = (n + 255) / 256;
     grid_prep_kernel<<<nb, 256, 0, st>>>(x, n, g, w.hkey, w.hcount, w.slot_of, w.pts4, w.status);
     w.marks->kernel("grid_prep", st);
-    const int cells_per_block = 256 * CELLS_PER_THREAD;
-    grid_cells_kernel<<<(unsigned)((H + cells_per_block - 1) / cells_per_block), 256, 0, st>>>(
-        (int)H, w.hkey, w.hcount, w.hpack, w.hcursor, w.cell_start, w.cell_count, w.cell_key, w.cell_rep, occ, w.ctr);
-    w.marks->kernel("grid_cells", st);
+    if ((e = launch_grid_cells(w, g, occ, st))) return e;
     // The neighbour lists need the cell table but not the grouped points.
     cudaStream_t s2 = fork(w, st, 0);
-    grid_nbr_kernel<<<152 * 16, 256, 0, s2>>>(g, w.ctr, w.cell_key, w.hpack, occ, w.nbr, w.ncnt);
-    w.marks->kernel("grid_nbrs", s2);
+    if ((e = launch_grid_nbrs(w, g, occ, s2))) return e;
     grid_scatter_kernel<<<nb, 256, 0, st>>>(n, w.slot_of, w.hcursor, w.hpack, w.pts4, w.spts, w.sidx, w.scell);
     w.marks->kernel("grid_scatter", st);
     join(w, st, s2, 1);
@@ -894,8 +895,30 @@ cudaError_t launch_grid_path(const DbWork &w, const GridGeom &g, const float *x,
     }
 }
 
-cudaError_t launch_grid_candidates(const DbWork &w, const GridGeom &g, int64_t /*n*/, cudaStream_t st) {
-    grid_candidates_kernel<<<152 * 4, 256, 0, st>>>(g, w.ctr, w.cell_count, w.nbr, w.ncnt, w.ctr + 1);
+cudaError_t launch_grid_cells(const DbWork &w, const GridGeom &g, unsigned *occ, cudaStream_t st) {
+    int64_t H = int64_t(1) << g.hbits;
+    if (g.dense) {
+        H = 1;
+        for (int k = 0; k < g.d; ++k) H *= g.G;
+    }
+    const int cells_per_block = 256 * CELLS_PER_THREAD;
+    grid_cells_kernel<<<(unsigned)((H + cells_per_block - 1) / cells_per_block), 256, 0, st>>>(
+        (int)H, g.dense, w.hkey, w.hcount, w.hpack, w.hcursor, w.cell_start, w.cell_count, w.cell_key, w.cell_rep,
+        occ, w.ctr);
+    w.marks->kernel("grid_cells", st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grid_nbrs(const DbWork &w, const GridGeom &g, const unsigned *occ, cudaStream_t st) {
+    grid_nbr_kernel<<<152 * 16, 256, 0, st>>>(g, w.ctr, w.cell_key, w.hpack, occ, w.nbr, w.ncnt);
+    w.marks->kernel("grid_nbrs", st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grid_candidates(const DbWork &w, const GridGeom &g, int64_t /*n*/, bool own_cell_listed,
+                                   cudaStream_t st) {
+    grid_candidates_kernel<<<152 * 4, 256, 0, st>>>(g, w.ctr, w.cell_count, w.nbr, w.ncnt, own_cell_listed ? 1 : 0,
+                                                    w.ctr + 1);
     w.marks->kernel("grid_candidates", st);
     return cudaGetLastError();
 }

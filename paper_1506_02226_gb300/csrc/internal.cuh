@@ -21,9 +21,10 @@
 //   0 grid cells|points, 1 grid candidate pairs, 2..5 core/border/noise/clusters,
 //   6 band pairs rechecked, 7..8 band verification, 9..13 pipeline diagnostics,
 //   16..19 pair tests evaluated by the count, merge, border and (grid path)
-//   outer-ring merge passes.
+//   outer-ring merge passes, 31 work items of the projected grid (int).
 #define DB_NCTR 32
 #define DB_CTR_EVAL 16
+#define DB_CTR_MID_ITEMS 31
 #define DB_HASH_EMPTY 0xffffffffu
 
 namespace db {
@@ -93,6 +94,13 @@ __device__ __forceinline__ int uf_unite_root(int *parent, int a, int b, unsigned
     }
     atomicOr(status, DB_EBIT_TIMEOUT);
     return -1;
+}
+
+// Cell hash slot of the grid paths: four consecutive keys (four cells in a
+// row along x) share one 32-byte bucket of the packed table, so the lookups of
+// a cell's x-neighbours, made by neighbouring lanes, touch few sectors.
+__device__ __forceinline__ unsigned hash_slot(unsigned key, int bits) {
+    return ((((key >> 2) * 2654435761u) >> (34 - bits)) << 2) | (key & 3u);
 }
 
 // 2^-10 grid check of one coordinate: finite, 0 <= x < 1, 1024 x integral.
@@ -209,6 +217,7 @@ struct DbWork {
 // Host-side grid geometry for d <= 3 (see grid.cu).
 struct GridGeom {
     int32_t d, c, G, Tc, noff, nnear, hbits;
+    int32_t dense;  // 1: cells indexed directly by key (slot = key, G^d slots), 0: hashed (2^hbits slots)
     float Tp1;
     char4 off[124];
 };
@@ -231,6 +240,19 @@ bool grid_geometry(int32_t d, int64_t Tc, int64_t n, GridGeom *g);
 cudaError_t launch_grid_path(const DbWork &w, const GridGeom &g, const float *x, int64_t n, int32_t min_pts,
                              bool exact_counts, int32_t *labels, int32_t *counts_out, uint8_t *core_out,
                              cudaStream_t st);
-cudaError_t launch_grid_candidates(const DbWork &w, const GridGeom &g, int64_t n, cudaStream_t st);
+// Ordered candidate pairs of a grid run (own cell listed: the projected grid).
+cudaError_t launch_grid_candidates(const DbWork &w, const GridGeom &g, int64_t n, bool own_cell_listed,
+                                   cudaStream_t st);
+// Structure kernels shared by the eps-grid and the projected grid (grid_mid.cu):
+// occupied slots -> cell table (ids, ranges, keys, occupancy bits), and the
+// neighbour-cell lists of g's offsets.
+cudaError_t launch_grid_cells(const DbWork &w, const GridGeom &g, unsigned *occ, cudaStream_t st);
+cudaError_t launch_grid_nbrs(const DbWork &w, const GridGeom &g, const unsigned *occ, cudaStream_t st);
+// Projected grid for 4 <= d <= 8 (grid_mid.cu): geometry (false when the
+// cells would be too coarse to prune) and the whole path.
+bool mid_geometry(int32_t d, int64_t Tc, int64_t n, GridGeom *g);
+cudaError_t launch_mid_grid_path(const DbWork &w, const GridGeom &g, const float *x, int64_t n, int32_t d,
+                                 int32_t min_pts, bool exact_counts, int32_t *labels, int32_t *counts_out,
+                                 uint8_t *core_out, cudaStream_t st);
 cudaError_t launch_stats(const DbWork &w, int64_t n, const int32_t *labels, cudaStream_t st);
 int32_t dp_for(int32_t d);

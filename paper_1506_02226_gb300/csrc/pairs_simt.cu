@@ -5,7 +5,7 @@
 // inner loop; Section IV-B fuses the distance test with the neighbour count, so
 // the distance matrix is never stored; Section IV-B's last step moves the
 // per-row terms out of the loop (the Gram form
-// dist = |t|^2 + |p|^2 - 2 t.p).  Here a 256-thread block owns a 64x64 tile of
+// dist = |t|^2 + |p|^2 - 2 t.p), used here up to d = 16.  Here a 256-thread block owns a 64x64 tile of
 // (row, column) pairs; each thread scores a 4x4 micro-tile from shared memory.
 // The same tile loop feeds three consumers:
 //   PASS_COUNT   neighbour counts (step 2, core detection)
@@ -14,10 +14,15 @@
 //
 // Exact arithmetic.  The score of a pair is T + 1 - D(p,q), an integer, and q
 // is a neighbour iff score >= 1; __saturatef(score) is then exactly 0 or 1.
-//   MODE_GRAM   (d <= 8): score = (T+1 - |p|^2) - |q|^2 + sum_k (2u_pk) u_qk in
-//               FP32.  Every partial sum is an integer of magnitude below
-//               2*d*1023^2 <= 16,744,464 < 2^24, so FP32 holds it exactly.
-//   MODE_DIRECT (FP32, d <= 16, or T + 1 <= 2^24): score = (T+1) - sum (u_pk-u_qk)^2.
+// Rows hold centred units v = u - 512 in [-512, 511] (D is unchanged).
+//   MODE_GRAM   (d <= 16): score = (T+1 - |p|^2) - |q|^2 + sum_k (2v_pk) v_qk
+//               in FP32 (Section IV-B's hoisted form).  After k terms the
+//               partial sum lies in [T+1 - sum_i (|v_pi| + |v_qi|)^2, T+1] (the
+//               terms not yet added are sums of squares, and each one added is
+//               at least -(|v_pi| + |v_qi|)^2 + v_pi^2 + v_qi^2), and
+//               (|v_pi| + |v_qi|)^2 <= 1023^2, so every partial sum is an
+//               integer of magnitude below 16 * 1023^2 < 2^24: FP32 is exact.
+//   MODE_DIRECT (FP32, T + 1 <= 2^24): score = (T+1) - sum (v_pk-v_qk)^2.
 //               Partial sums only decrease; they are exact while >= -2^24, and
 //               once below that they stay below 1, so the decision is exact.
 //   MODE_INT    otherwise: the same in int32.
@@ -39,7 +44,7 @@ __global__ void prep_dense_kernel(const float *__restrict__ x, int64_t n, int d,
         if (k < d) {
             int u;
             bad |= !db::on_grid(x[r * d + k], u);
-            v = (float)u;
+            v = (float)(u - 512);  // centred: exact Gram form up to d = 16
         }
         P[i] = v;
     }
@@ -89,7 +94,7 @@ cudaError_t run_passes(ApArgs a, const DbWork &w, int n, int min_pts, cudaStream
 
 template <int DP>
 cudaError_t dispatch_mode(int mode, ApArgs a, const DbWork &w, int n, int min_pts, cudaStream_t st) {
-    if constexpr (DP <= 8) {
+    if constexpr (DP <= 16) {
         return run_passes<DP, MODE_GRAM>(a, w, n, min_pts, st);
     } else {
         if (mode == MODE_DIRECT) return run_passes<DP, MODE_DIRECT>(a, w, n, min_pts, st);
@@ -143,7 +148,7 @@ cudaError_t launch_allpairs_simt(const DbWork &w, int64_t n64, int32_t d, int32_
     // Enough blocks to fill 152 SMs a few times over, splitting the column range.
     int splits = (4 * 152 + a.ntiles - 1) / a.ntiles;
     a.splits = std::max(1, std::min(splits, a.ntiles));
-    int mode = (d <= 8) ? MODE_GRAM : ((d <= 16 || Tc + 1 <= (1 << 24)) ? MODE_DIRECT : MODE_INT);
+    int mode = (d <= 16) ? MODE_GRAM : ((Tc + 1 <= (1 << 24)) ? MODE_DIRECT : MODE_INT);
     switch (dp) {
         case 1: return dispatch_mode<1>(mode, a, w, n, min_pts, st);
         case 2: return dispatch_mode<2>(mode, a, w, n, min_pts, st);

@@ -107,6 +107,31 @@ def large_lowd(d: int = 2, n: int = 500_000, seed: int | None = None) -> Instanc
     return Instance(pts, float(np.float32(0.005)), 10)
 
 
+def mid_d(d: int = 8, n: int = 200_000, seed: int | None = None) -> Instance:
+    """4 <= d <= 8 (the projected-grid path): the d <= 3 recipe's 50 blobs, sigma
+    log-uniform in [0.002, 0.02] per coordinate, 20% noise, with eps scaled to
+    the dimension, 0.005 * sqrt(d / 2) (the typical distance of two points of a
+    blob grows as sqrt(d)), min_pts 10."""
+    if not 4 <= d <= 8:
+        raise ValueError("mid_d is the 4 <= d <= 8 recipe")
+    if seed is None:
+        seed = SEED_BASE + 6 + 100 * d
+    rng = np.random.default_rng(seed)
+    sig = np.exp(rng.uniform(math.log(0.002), math.log(0.02), size=50))
+    pts = blobs_plus_noise(rng, n, d, sig, 0.20)
+    return Instance(pts, float(np.float32(0.005 * math.sqrt(d / 2))), 10)
+
+
+def paper_3d(n: int = 23_040, seed: int = SEED_BASE + 7) -> Instance:
+    """A stand-in for the paper's unnamed 3-D point set at its middle size
+    (N = 23,040, Section V): the d <= 3 recipe (50 blobs, sigma log-uniform in
+    [0.002, 0.02], 20% noise) with eps 0.02 and min_pts 10 (the paper gives
+    neither)."""
+    rng = np.random.default_rng(seed)
+    sig = np.exp(rng.uniform(math.log(0.002), math.log(0.02), size=50))
+    return Instance(blobs_plus_noise(rng, n, 3, sig, 0.20), float(np.float32(0.02)), 10)
+
+
 # eps of the d=64 workload: the median over 2,000 seeded query points of the
 # distance to the 30th nearest point (the query itself counted), rounded to
 # float32.  Written by ``derive_highd_eps()`` below and frozen here.

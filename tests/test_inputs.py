@@ -38,3 +38,12 @@ def test_batch_and_serve_recipes():
     assert 1000 <= job.n <= 500_000 and job.d in (2, 3, 32) and _on_grid(job.points)
     t = inputs.serve_arrivals(100, 50.0)
     assert np.all(np.diff(t) > 0)
+
+
+@pytest.mark.parametrize("d", [4, 8])
+def test_mid_d_recipe(d):
+    inst = inputs.mid_d(d, n=20_000)
+    assert inst.points.shape == (20_000, d) and _on_grid(inst.points)
+    assert inst.min_pts == 10 and inst.eps == float(np.float32(0.005 * np.sqrt(d / 2)))
+    with pytest.raises(ValueError):
+        inputs.mid_d(3)
