@@ -60,7 +60,7 @@ extern "C" {
 #define DBSCAN_ERR_TIMEOUT 5       /* a bounded device-side wait or a host wait expired */
 #define DBSCAN_ERR_BUSY 6          /* serve admission is full (slots or HBM budget) */
 #define DBSCAN_ERR_UNSUPPORTED 7   /* option or shape this build does not handle; also n above 2^29 on the
-                                      eps-grid path or above 2^25 on the all-pairs paths (int32 index ranges) */
+                                      grid paths or above 2^25 on the all-pairs paths (int32 index ranges) */
 #define DBSCAN_ERR_NOT_FOUND 8     /* unknown serve job id */
 
 /* Pair-test arithmetic. */
@@ -129,7 +129,11 @@ typedef struct dbscan_stats {
  * max_d 64, PREC_AUTO, GRID_AUTO, LABEL_ROOT_INDEX. */
 void dbscan_opts_default(dbscan_opts *opts);
 
-/* Creates a plan and allocates its device workspace for (max_n, max_d).
+/* Creates a plan and allocates its device workspace for (max_n, max_d): the
+ * point rows of Section IV-A (packed, the paper's point[3][N] layout idea),
+ * the neighbour counts and core flags of Section IV-B (its `valid` vector),
+ * the union-find forest that replaces Section IV-C's cluster matrix, and the
+ * candidate structures of the grid paths.
  * *out receives the plan; on error *out is NULL.  DBSCAN_ERR_OOM if the
  * workspace does not fit. */
 int dbscan_plan_create(dbscan_plan **out, const dbscan_opts *opts);
@@ -242,9 +246,11 @@ typedef struct dbscan_instance {
     int32_t *labels_out; /* device int32 [n]; labels are local indices 0..n-1 of this instance */
 } dbscan_instance;
 
-/* Clusters `count` independent instances (each as dbscan_run would, with the
- * plan's label mode; all-pairs SIMT arithmetic, 1 <= d <= 16, larger d gives
- * DBSCAN_ERR_UNSUPPORTED).  All instances run in one graph-captured launch
+/* Clusters `count` independent instances, each by Section I's three steps as
+ * dbscan_run would (with the plan's label mode; the all-pairs CUDA-core tile
+ * of Sections IV-A/IV-B, 1 <= d <= 16, larger d gives
+ * DBSCAN_ERR_UNSUPPORTED).  Batching many instances into one launch sequence
+ * is this library's addition: the paper clusters one point set.  All instances run in one graph-captured launch
  * sequence of persistent kernels that share a work queue of (instance, row
  * tile, column chunk) items.  The first call autotunes the chunk size and grid
  * on the given batch.  Uses its own device workspace, grown on demand and kept
@@ -308,7 +314,8 @@ void dbscan_serve_opts_default(dbscan_serve_opts *opts);
  * for later jobs.  The serving form of the paper's method has no counterpart
  * in the paper: it is the continuous-batching server this library adds. */
 int dbscan_serve_create(dbscan_server **out, const dbscan_serve_opts *opts);
-/* Queues a job (Section I's three steps on one instance, as dbscan_run).  The
+/* Queues a job (Section I's three steps on one instance, as dbscan_run; the
+ * server around it has no counterpart in the paper).  The
  * instance's device buffers must stay valid until it is done.  *job_id
  * receives its id.  DBSCAN_ERR_ARG for a bad instance or n > max_n / d >
  * max_d; DBSCAN_ERR_BUSY when max_queue jobs already wait.  Thread-safe. */
