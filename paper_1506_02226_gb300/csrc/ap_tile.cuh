@@ -60,10 +60,23 @@ __device__ __forceinline__ void ap_tile_body(const ApArgs &a, int rt, int ct_beg
     __syncthreads();  // the previous work item of this block is done with the tiles
 
     // ---- the row tile stays in shared memory for the whole block (Section IV-A) ----
-    for (int e = tid; e < BM * DP; e += NT) {
-        int r = e / DP, k = e - (e / DP) * DP;
-        int row = row0 + r;
-        As[k][r] = (row < a.n) ? a.P[(size_t)row * DP + k] : 0.f;
+    if constexpr (DP % 4 == 0) {  // rows of 4, 8 or 16 units: 16-byte vector loads (rows are 16-byte aligned)
+        for (int e = tid; e < BM * (DP / 4); e += NT) {
+            const int r = e / (DP / 4), k4 = e - r * (DP / 4);
+            const int row = row0 + r;
+            const float4 v = (row < a.n) ? reinterpret_cast<const float4 *>(a.P + (size_t)row * DP)[k4]
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+            As[4 * k4][r] = v.x;
+            As[4 * k4 + 1][r] = v.y;
+            As[4 * k4 + 2][r] = v.z;
+            As[4 * k4 + 3][r] = v.w;
+        }
+    } else {
+        for (int e = tid; e < BM * DP; e += NT) {
+            int r = e / DP, k = e - (e / DP) * DP;
+            int row = row0 + r;
+            As[k][r] = (row < a.n) ? a.P[(size_t)row * DP + k] : 0.f;
+        }
     }
     if (PASS != PASS_COUNT)
         for (int r = tid; r < BM; r += NT) Ac[r] = (row0 + r < a.n) ? a.core[row0 + r] : 0;
@@ -122,11 +135,26 @@ __device__ __forceinline__ void ap_tile_body(const ApArgs &a, int rt, int ct_beg
                 const int col = col0 + tid;
                 float nrm = 0.f;
                 if (col < a.n) {
+                    if constexpr (DP % 4 == 0) {  // 16-byte vector loads of the column's units
 #pragma unroll
-                    for (int k = 0; k < DP; ++k) {
-                        float v = a.P[(size_t)col * DP + k];
-                        Bs[k][tid] = v;
-                        nrm = fmaf(v, v, nrm);
+                        for (int k4 = 0; k4 < DP / 4; ++k4) {
+                            const float4 v = reinterpret_cast<const float4 *>(a.P + (size_t)col * DP)[k4];
+                            Bs[4 * k4][tid] = v.x;
+                            Bs[4 * k4 + 1][tid] = v.y;
+                            Bs[4 * k4 + 2][tid] = v.z;
+                            Bs[4 * k4 + 3][tid] = v.w;
+                            nrm = fmaf(v.x, v.x, nrm);
+                            nrm = fmaf(v.y, v.y, nrm);
+                            nrm = fmaf(v.z, v.z, nrm);
+                            nrm = fmaf(v.w, v.w, nrm);
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < DP; ++k) {
+                            float v = a.P[(size_t)col * DP + k];
+                            Bs[k][tid] = v;
+                            nrm = fmaf(v, v, nrm);
+                        }
                     }
                     Bn[tid] = -nrm;
                 } else {

@@ -335,7 +335,7 @@ int64_t build_table(const dbscan_instance *inst, int count, int ch, BInst *t, in
         I.item0 = (int)items;
         I.pad = 0;
         base += in.n;
-        poff += in.n * I.dp;
+        poff += (in.n * I.dp + 3) / 4 * 4;  // 16-byte aligned rows of every instance (vector tile loads)
         items += (int64_t)I.ntiles * I.nchunks;
     }
     *points = base;

@@ -44,8 +44,9 @@
 //               K/16 tcgen05.mma (M=128, N=256, K=16) per tile into one of two
 //               256-column accumulators; tcgen05.commit signals the epilogue
 //   warps 2..   epilogue: tcgen05.ld of the accumulator (one TMEM lane = one
-//               row; two or four warps per lane quadrant split the 256
-//               columns), the
+//               row; in the FP16 count one warp per lane quadrant and tile,
+//               the two accumulator buffers served by two groups; otherwise
+//               two or four warps per lane quadrant split the 256 columns), the
 //               exact decision above, and the pass's consumer: neighbour count,
 //               union of core-core neighbours, or smallest core neighbour.
 // Every wait is bounded (about two seconds of %globaltimer); on expiry the CTA
@@ -69,13 +70,16 @@ __host__ __device__ constexpr int bf16_band(int K) { return 16 * K; }
 
 enum { TC_COUNT = 0, TC_UNION = 1, TC_BORDER = 2, TC_VERIFY = 3 };
 
-// Epilogue warps per CTA.  The FP16 count: two per TMEM lane quadrant, each
-// loading its 128 accumulator columns at once and deciding them in one pass
-// (fewer per-tile synchronisations per pair than four warps of 64 columns,
-// which measured 7% slower).  Merge, border and BF16: four per quadrant (64
-// columns each, in groups of 32: the candidate scores and the accumulator copy
-// fit the 16-warp register budget).  Verification: two per quadrant, groups
-// of 64.
+// Epilogue warps per CTA.  The FP16 count: two groups of four warps (one per
+// TMEM lane quadrant) take alternate tiles, one group per accumulator buffer,
+// and each warp decides all 256 columns of its rows, loading 32 columns ahead
+// of the ones it decides; the two groups' phases drift apart, so one group's
+// loads overlap the other's arithmetic (measured against the alternatives: four
+// warps of 64 columns per quadrant 6.75 ms, two of 128 on every tile 6.27,
+// this 6.14, sixteen warps in two groups 6.30).  Merge, border and BF16: four
+// per quadrant (64 columns each, in groups of 32: the candidate scores and the
+// accumulator copy fit the 16-warp register budget).  Verification: two per
+// quadrant, groups of 64.
 template <int PASS, bool BF16>
 constexpr int epi_warps() {
     return (PASS == TC_COUNT && !BF16) ? 8 : (PASS != TC_VERIFY ? 16 : 8);
@@ -270,6 +274,19 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// Waits for this thread's TMEM loads; the registers of r pass through the
+// statement, so no use of them can be scheduled before the wait.
+__device__ __forceinline__ void tmem_wait_ld_dep(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+
 // 32 consecutive accumulator columns of this thread's TMEM lane (no wait).
 __device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t *r) {
     asm volatile(
@@ -383,6 +400,9 @@ __device__ __noinline__ int unite_root(int *parent, int p, int q, unsigned *stat
 template <int PASS, bool BF16>
 __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(TcArgs a) {
     constexpr int EPI_WARPS = epi_warps<PASS, BF16>();
+    // FP16 count: two groups of four warps take alternate tiles (a group per accumulator buffer)
+    constexpr int EPI_GROUPS = (PASS == TC_COUNT && !BF16) ? 2 : 1;
+    constexpr int TILE_WARPS = EPI_WARPS / EPI_GROUPS;  // epilogue warps that read one tile
     constexpr int GW = group_cols<PASS, BF16>();    // columns per group
     constexpr int NG = (1024 / EPI_WARPS) / GW;     // groups per epilogue warp and tile
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -405,11 +425,11 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
             mbar_init(&S.a_full[i], 1);
             mbar_init(&S.a_empty[i], 1 + EPI_WARPS);
             mbar_init(&S.t_full[i], 1);
-            mbar_init(&S.t_empty[i], EPI_WARPS);
+            mbar_init(&S.t_empty[i], TILE_WARPS);
         }
         for (int i = 0; i < NSTAGE; ++i) {
             mbar_init(&S.b_full[i], 1);
-            mbar_init(&S.b_empty[i], 1 + EPI_WARPS);
+            mbar_init(&S.b_empty[i], 1 + TILE_WARPS);
         }
         mbar_init(&S.drain, 1);
         S.abort_flag = 0;
@@ -568,6 +588,7 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
             bool ok = true;
             for (int ct = c0; ct < c1; ++ct, ++t) {
                 const int s = t % NSTAGE, b = t & 1;
+                if (EPI_GROUPS == 2 && b != (ew >> 2)) continue;  // the other group's tile
                 // warp-uniform outcome: the accumulator loads below are warp-collective
                 // the accumulator is usually ready: test once inline before the bounded wait
                 if (!__all_sync(0xffffffffu,
@@ -590,6 +611,61 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
                         if (q >= 0) pr[k] = db::ld_relaxed(a.parent + q);
                     }
                 }
+                if constexpr (PASS == TC_COUNT && !BF16) {
+                    // all 256 columns in eight groups of 32: the next group's TMEM load
+                    // is in flight while this group is decided
+                    const uint32_t tb = tmem + lane_base + (uint32_t)(b * TN);
+                    const float c1 = 1.f - alpha;
+                    const unsigned long long m2 = f2_pack(-2.f, -2.f);
+                    unsigned long long acc[4] = {0ull, 0ull, 0ull, 0ull};
+                    uint32_t ga[32], gb[32];
+                    auto decide = [&](uint32_t (&g)[32], const float *bet) {
+#pragma unroll
+                        for (int j8 = 0; j8 < 4; ++j8) {
+                            const float4 ba = *reinterpret_cast<const float4 *>(bet + 8 * j8);
+                            const float4 bb = *reinterpret_cast<const float4 *>(bet + 8 * j8 + 4);
+                            const float bq[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
+#pragma unroll
+                            for (int h = 0; h < 4; ++h) {
+                                const unsigned long long w = f2_fma(
+                                    f2_pack(__uint_as_float(g[8 * j8 + 2 * h]), __uint_as_float(g[8 * j8 + 2 * h + 1])),
+                                    m2, f2_pack(bq[2 * h], bq[2 * h + 1]));
+                                float w0, w1;
+                                f2_unpack(w, w0, w1);
+                                acc[h] = f2_add(acc[h], f2_pack(__saturatef(c1 - w0), __saturatef(c1 - w1)));
+                            }
+                        }
+                    };
+                    const float *b0 = S.metaB[s][0].beta, *b1 = S.metaB[s][1].beta;
+                    tmem_ld32_nowait(tb, ga);
+                    tmem_wait_ld_dep(ga);
+                    tmem_ld32_nowait(tb + 32, gb);
+                    decide(ga, b0);
+                    tmem_wait_ld_dep(gb);
+                    tmem_ld32_nowait(tb + 64, ga);
+                    decide(gb, b0 + 32);
+                    tmem_wait_ld_dep(ga);
+                    tmem_ld32_nowait(tb + 96, gb);
+                    decide(ga, b0 + 64);
+                    tmem_wait_ld_dep(gb);
+                    tmem_ld32_nowait(tb + 128, ga);
+                    decide(gb, b0 + 96);
+                    tmem_wait_ld_dep(ga);
+                    tmem_ld32_nowait(tb + 160, gb);
+                    decide(ga, b1);
+                    tmem_wait_ld_dep(gb);
+                    tmem_ld32_nowait(tb + 192, ga);
+                    decide(gb, b1 + 32);
+                    tmem_wait_ld_dep(ga);
+                    tmem_ld32_nowait(tb + 224, gb);
+                    decide(ga, b1 + 64);
+                    tmem_wait_ld_dep(gb);
+                    decide(gb, b1 + 96);
+                    float sm[8];
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) f2_unpack(acc[h], sm[2 * h], sm[2 * h + 1]);
+                    if (row_ok) cnt += (int)(((sm[0] + sm[1]) + (sm[2] + sm[3])) + ((sm[4] + sm[5]) + (sm[6] + sm[7])));
+                } else
 #pragma unroll 1
                 for (int hc = 0; hc < NG; ++hc) {
                     const int cb = moff + hc * GW;  // column within the 128-column block
