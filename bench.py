@@ -613,6 +613,7 @@ def run_batch(args, steps=None):
     if B.dbscan_batch(plan.handle, arr, st) != 0:  # autotune + graph capture
         raise RuntimeError("dbscan_batch failed")
     ch, bps = B.dbscan_batch_config(plan.handle)
+    tile_rows, tile_cols = B.dbscan_batch_tile(plan.handle)
     ncore = [st[k].n_core for k in range(count)]
     pair_tests = sum(st[k].pair_tests for k in range(count))  # device counters of that call
     pass_pairs = B.dbscan_plan_counters(plan.handle)[16:19]  # that call's totals per pass
@@ -701,7 +702,8 @@ def run_batch(args, steps=None):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"batch: {count} instances, n log-uniform 64..8192, d in {{2,3,16}}, 1-8 blobs + 10% "
                                "noise, eps U[0.01,0.05], min_pts U{4..16}", "points": int(loffs[-1]),
-                   "path": "all-pairs SIMT, one graph launch", "autotuned": {"chunk_tiles": ch, "blocks_per_sm": bps},
+                   "path": "all-pairs SIMT, one graph launch",
+                   "autotuned": {"tile": [tile_rows, tile_cols], "chunk_tiles": ch, "blocks_per_sm": bps},
                    "l2": "flushed by a 256 MiB write before every timed step"},
         "pair_tests_per_step": pair_tests, "pair_tests_per_s": pair_tests / (ms * 1e-3),
         "all_pairs_per_step": pairs,

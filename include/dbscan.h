@@ -256,8 +256,9 @@ typedef struct dbscan_instance {
  * on the given batch.  Uses its own device workspace, grown on demand and kept
  * by the plan.  Synchronous; per_inst (host, nullable, `count` entries)
  * receives per-instance counts.  DBSCAN_ERR_ARG above 2^30 points in all;
- * DBSCAN_ERR_UNSUPPORTED when the work items (64-point row tiles x column
- * chunks, about n^2 / 16,384 per instance) exceed 2^31.  With per_inst given,
+ * DBSCAN_ERR_UNSUPPORTED when the work items (32-point row tiles x column
+ * chunks of four 64-point tiles, the finest shape the autotuner tries: about
+ * n^2 / 8,192 per instance) exceed 2^31.  With per_inst given,
  * each entry's pair_tests counts the instance's evaluated pair predicates and
  * the plan's counters 16..18 (dbscan_plan_counters) hold the batch's totals
  * for the count, merge and border passes. */
@@ -267,6 +268,11 @@ int dbscan_batch(dbscan_plan *plan, const dbscan_instance *inst, int32_t count, 
  * call: column tiles (64 points each) per work item and resident blocks per SM.
  * DBSCAN_ERR_NOT_FOUND before the first batch. */
 int dbscan_batch_config(dbscan_plan *plan, int32_t *chunk_tiles, int32_t *blocks_per_sm);
+
+/* The tile shape dbscan_batch's autotuner picked with that configuration:
+ * rows per row tile (32, 64 or 128) by 64 columns per column tile.
+ * DBSCAN_ERR_NOT_FOUND before the first batch. */
+int dbscan_batch_tile(dbscan_plan *plan, int32_t *tile_rows, int32_t *tile_cols);
 
 /* ---- Served form: continuous batching of submitted jobs under an HBM budget ---- */
 

@@ -97,6 +97,7 @@ _SIGS = {
     "dbscan_plan_phase_times": (ctypes.c_int, [c_p, c_i32, c_p, c_p, c_p]),
     "dbscan_batch": (ctypes.c_int, [c_p, c_p, c_i32, c_p]),
     "dbscan_batch_config": (ctypes.c_int, [c_p, c_p, c_p]),
+    "dbscan_batch_tile": (ctypes.c_int, [c_p, c_p, c_p]),
     "dbscan_serve_opts_default": (None, [c_p]),
     "dbscan_serve_create": (ctypes.c_int, [c_p, c_p]),
     "dbscan_serve_submit": (ctypes.c_int, [c_p, c_p, c_p]),
@@ -255,6 +256,12 @@ def dbscan_batch_config(plan: int) -> tuple[int, int]:
     ch, bps = c_i32(), c_i32()
     _check(lib().dbscan_batch_config(plan, ctypes.byref(ch), ctypes.byref(bps)), "dbscan_batch_config")
     return ch.value, bps.value
+
+
+def dbscan_batch_tile(plan: int) -> tuple[int, int]:
+    rows, cols = c_i32(), c_i32()
+    _check(lib().dbscan_batch_tile(plan, ctypes.byref(rows), ctypes.byref(cols)), "dbscan_batch_tile")
+    return rows.value, cols.value
 
 
 def dbscan_serve_opts_default() -> dbscan_serve_opts:

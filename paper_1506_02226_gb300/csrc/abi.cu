@@ -78,6 +78,7 @@ size_t layout(DbWork &w, const dbscan_opts &o, char *base) {
         w.noff_cap = dg == 1 ? 4 : (dg == 2 ? 24 : 124);
         w.nbr = c.take<int32_t>((size_t)n * w.noff_cap);
         w.ncnt = c.take<int32_t>(n);
+        w.cell_cand = c.take<int32_t>(n);
     } else {
         w.hcap = 0;
         w.noff_cap = 0;

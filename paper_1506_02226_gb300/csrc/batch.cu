@@ -35,9 +35,11 @@ struct BInst {
     int min_pts;
     int base;       // first batch point of this instance
     long long poff; // first float of its packed rows
-    int ntiles;     // ceil(n / 64)
-    int nchunks;    // ceil(ntiles / CH)
+    int ntiles;     // row tiles of 16 * RM points
+    int ctiles;     // column tiles of 64 points
+    int nchunks;    // ceil(ctiles / CH)
     int item0;      // first work item of this instance
+    int box0[3];    // its first tile box of 32, 64 and 128 rows
     int pad;
 };
 
@@ -45,7 +47,8 @@ struct BHdr {  // device-side sizes of the current batch
     int count;
     int total_points;
     int total_items;
-    int pad;
+    int box_level0[3];  // first box of each level (32, 64, 128 rows) in the box array
+    int pad[2];
 };
 
 __device__ __forceinline__ int find_inst_by_base(const BInst *__restrict__ t, int count, int g) {
@@ -68,32 +71,119 @@ __device__ __forceinline__ int find_inst_by_item(const BInst *__restrict__ t, in
     return lo;
 }
 
-__global__ void batch_prep_kernel(const BInst *__restrict__ t, const BHdr *__restrict__ hdr, int *__restrict__ pinst,
-                                  float *__restrict__ P, unsigned *status) {
-    const int count = hdr->count, total = hdr->total_points;
+// Morton (Z-order) dilation of a 10-bit coordinate: bit b moves to bit 3b.
+__device__ __forceinline__ unsigned dilate3(unsigned v) {
+    v &= 1023u;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+// One block per instance at a time.  An instance of 2 .. sort_cap points is
+// put in Z-order of its first three grid coordinates (a bitonic sort of
+// {code, index} keys in shared memory), so that a 64-row tile covers a small
+// region; larger ones keep their order.  Then the rows are packed in that order
+// (centred units v = u - 512: the Gram form is exact up to d = 16), perm gets
+// the point of each row, and each 64-row tile its box: the least and greatest
+// unit of its rows on every axis.  The reordering changes no result: every
+// pass decides the same pairs, and labels are by point index.
+__global__ void __launch_bounds__(1024) batch_sortpack_kernel(const BInst *__restrict__ t,
+                                                              const BHdr *__restrict__ hdr, int sort_cap,
+                                                              int *__restrict__ pinst, int *__restrict__ perm,
+                                                              float *__restrict__ P, float *__restrict__ tbox,
+                                                              unsigned *status) {
+    extern __shared__ unsigned long long keys[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int count = hdr->count;
     bool bad = false;
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
-        const int i = find_inst_by_base(t, count, g);
-        const BInst &I = t[i];
-        const int loc = g - I.base;
-        pinst[g] = i;
-        float *row = P + I.poff + (long long)loc * I.dp;
-        for (int k = 0; k < I.dp; ++k) {
-            float v = 0.f;
-            if (k < I.d) {
-                int u;
-                bad |= !db::on_grid(I.x[(size_t)loc * I.d + k], u);
-                v = (float)(u - 512);  // centred units: the Gram form is exact up to d = 16
+    for (int i = blockIdx.x; i < count; i += gridDim.x) {
+        const BInst I = t[i];
+        const int n = I.n, d = I.d, dp = I.dp;
+        const bool sorted = n > 1 && n <= sort_cap;
+        if (sorted) {
+            int npow = 2;
+            while (npow < n) npow <<= 1;
+            const int dz = d < 3 ? d : 3;
+            for (int s = tid; s < npow; s += blockDim.x) {
+                unsigned long long k = ~0ull;
+                if (s < n) {
+                    unsigned code = 0;
+                    for (int j = 0; j < dz; ++j) {
+                        int u;
+                        db::on_grid(I.x[(size_t)s * d + j], u);  // off-grid input is reported below
+                        code |= dilate3((unsigned)u) << j;
+                    }
+                    k = ((unsigned long long)code << 32) | (unsigned)s;
+                }
+                keys[s] = k;
             }
-            row[k] = v;
+            __syncthreads();
+            for (int k = 2; k <= npow; k <<= 1)
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    for (int x = tid; x < npow; x += blockDim.x) {
+                        const int y = x ^ j;
+                        if (y > x) {
+                            const unsigned long long kx = keys[x], ky = keys[y];
+                            if ((kx > ky) == ((x & k) == 0)) {
+                                keys[x] = ky;
+                                keys[y] = kx;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
         }
+        for (int s = tid; s < n; s += blockDim.x) {
+            perm[I.base + s] = sorted ? (int)(unsigned)keys[s] : s;
+            pinst[I.base + s] = i;
+        }
+        for (int e = tid; e < n * dp; e += blockDim.x) {
+            const int s = e / dp, k = e - s * dp;
+            const int o = sorted ? (int)(unsigned)keys[s] : s;
+            float v = 0.f;
+            if (k < d) {
+                int u;
+                bad |= !db::on_grid(I.x[(size_t)o * d + k], u);
+                v = (float)(u - 512);
+            }
+            P[I.poff + (long long)s * dp + k] = v;
+        }
+        __syncthreads();  // the block's rows are visible to it; keys are free again
+        // boxes of the 32-, 64- and 128-row tiles, a warp per tile
+        for (int lv = 0; lv < 3; ++lv) {
+            const int rows = 32 << lv, nt = (n + rows - 1) / rows;
+            float *lvl = tbox + (size_t)(hdr->box_level0[lv] + I.box0[lv]) * 32;
+            for (int tt = warp; tt < nt; tt += nwarps) {
+                for (int k = 0; k < dp; ++k) {
+                    float lo = 3.0e38f, hi = -3.0e38f;
+                    for (int r = tt * rows + lane; r < min(n, (tt + 1) * rows); r += 32) {
+                        const float v = P[I.poff + (long long)r * dp + k];
+                        lo = fminf(lo, v);
+                        hi = fmaxf(hi, v);
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+                        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+                    }
+                    if (lane == 0) {
+                        lvl[(size_t)tt * 32 + k] = lo;
+                        lvl[(size_t)tt * 32 + 16 + k] = hi;
+                    }
+                }
+            }
+        }
+        __syncthreads();
     }
     if (bad) atomicOr(status, DB_EBIT_NOT_QUANTISED);
 }
 
-template <int PASS>
+template <int PASS, int RM>
 __global__ void __launch_bounds__(NT) batch_pass_kernel(const BInst *__restrict__ t, const BHdr *__restrict__ hdr,
-                                                        int ch_tiles, int *work, const float *P, int *count,
+                                                        int ch_tiles, int *work, const float *P,
+                                                        const int *perm, const float *tbox, int *count,
                                                         const uint8_t *core, int *parent, int *border,
                                                         unsigned *status, unsigned long long *ev) {
     __shared__ int item_s;
@@ -109,8 +199,8 @@ __global__ void __launch_bounds__(NT) batch_pass_kernel(const BInst *__restrict_
         const int k = item - I.item0;
         const int rt = k / I.nchunks, chunk = k - rt * I.nchunks;
         int ct0 = chunk * ch_tiles;
-        const int ct1 = min(I.ntiles, ct0 + ch_tiles);
-        if (PASS == PASS_UNION) ct0 = max(ct0, rt);
+        const int ct1 = min(I.ctiles, ct0 + ch_tiles);
+        if (PASS == PASS_UNION) ct0 = max(ct0, rt * RM / 4);  // the column tile of the row tile's first row
         if (ct0 >= ct1) continue;
         ApArgs a;
         a.P = P + I.poff;
@@ -126,13 +216,17 @@ __global__ void __launch_bounds__(NT) batch_pass_kernel(const BInst *__restrict_
         a.splits = 1;
         a.early = I.min_pts;  // batch outputs labels only: counts may stop at min_pts
         a.ev = ev ? ev + 3 * i : nullptr;  // pair tests evaluated by instance i's three passes
+        a.perm = perm + I.base;
+        constexpr int lv = RM == 2 ? 0 : (RM == 4 ? 1 : 2);  // box level of the row tiles
+        a.tbox = tbox + (size_t)(hdr->box_level0[1] + I.box0[1]) * 32;
+        a.tbox_rows = tbox + (size_t)(hdr->box_level0[lv] + I.box0[lv]) * 32;
         switch (I.dp) {  // block-uniform: one instance per work item
-            case 1: ap_tile_body<1, MODE_GRAM, PASS>(a, rt, ct0, ct1); break;
-            case 2: ap_tile_body<2, MODE_GRAM, PASS>(a, rt, ct0, ct1); break;
-            case 3: ap_tile_body<3, MODE_GRAM, PASS>(a, rt, ct0, ct1); break;
-            case 4: ap_tile_body<4, MODE_GRAM, PASS>(a, rt, ct0, ct1); break;
-            case 8: ap_tile_body<8, MODE_GRAM, PASS>(a, rt, ct0, ct1); break;
-            default: ap_tile_body<16, MODE_GRAM, PASS>(a, rt, ct0, ct1); break;
+            case 1: ap_tile_body<1, MODE_GRAM, PASS, RM>(a, rt, ct0, ct1); break;
+            case 2: ap_tile_body<2, MODE_GRAM, PASS, RM>(a, rt, ct0, ct1); break;
+            case 3: ap_tile_body<3, MODE_GRAM, PASS, RM>(a, rt, ct0, ct1); break;
+            case 4: ap_tile_body<4, MODE_GRAM, PASS, RM>(a, rt, ct0, ct1); break;
+            case 8: ap_tile_body<8, MODE_GRAM, PASS, RM>(a, rt, ct0, ct1); break;
+            default: ap_tile_body<16, MODE_GRAM, PASS, RM>(a, rt, ct0, ct1); break;
         }
     }
 }
@@ -149,24 +243,27 @@ __global__ void batch_core_init_kernel(const BInst *__restrict__ t, const BHdr *
     }
 }
 
-// Labels in each instance's own index space; per-instance counts
+// Labels in each instance's own index space (a thread per row: core flags
+// are by row, the forest and border choices by point); per-instance counts
 // (core, border, noise, clusters) when istats != nullptr; root flags for
-// compaction.
+// compaction, by point.
 __global__ void batch_label_kernel(const BInst *__restrict__ t, const BHdr *__restrict__ hdr,
-                                   const int *__restrict__ pinst, const uint8_t *__restrict__ core, int *parent,
-                                   const int *__restrict__ border, int *__restrict__ flags, int *istats) {
+                                   const int *__restrict__ pinst, const int *__restrict__ perm,
+                                   const uint8_t *__restrict__ core, int *parent, const int *__restrict__ border,
+                                   int *__restrict__ flags, int *istats) {
     const int total = hdr->total_points;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
         const int i = pinst[g];
         const BInst &I = t[i];
-        const int loc = g - I.base;
+        const int loc = perm[g];  // row g - base holds point loc
         int *par = parent + I.base;
+        const int bo = border[I.base + loc];
         int lab, kind;
         if (core[g]) {
             lab = db::uf_find(par, loc);
             kind = 0;
-        } else if (border[g] != DB_NONE) {
-            lab = db::uf_find(par, border[g]);
+        } else if (bo != DB_NONE) {
+            lab = db::uf_find(par, bo);
             kind = 1;
         } else {
             lab = -1;
@@ -174,7 +271,7 @@ __global__ void batch_label_kernel(const BInst *__restrict__ t, const BHdr *__re
         }
         I.labels[loc] = lab;
         const int root = (kind == 0 && lab == loc);
-        flags[g] = root;
+        flags[I.base + loc] = root;
         if (istats) {
             atomicAdd(istats + 4 * i + kind, 1);
             if (root) atomicAdd(istats + 4 * i + 3, 1);
@@ -194,18 +291,23 @@ __global__ void batch_compact_kernel(const BInst *__restrict__ t, const BHdr *__
 }
 
 constexpr int kCH[] = {4, 16, 64};
+constexpr int kRM[] = {2, 4, 8};  // row tiles of 32, 64 and 128 points (8 rows per thread for the last)
+constexpr int kSortMax = 16384;  // largest instance reordered (128 KiB of sort keys in shared memory)
 constexpr int kBPS[] = {4, 8};
 
 }  // namespace
 
 struct BatchState {
     int cap_count = 0;
-    int64_t cap_points = 0, cap_pfloats = 0;
+    int64_t cap_points = 0, cap_pfloats = 0, cap_tiles = 0;
     void *dev = nullptr;
     size_t dev_bytes = 0;
     BInst *d_table = nullptr;
     BHdr *d_hdr = nullptr;
     int *d_pinst = nullptr;
+    int *d_perm = nullptr;     // point of each row (rows of an instance in Z-order)
+    float *d_tbox = nullptr;   // per 64-row tile: least and greatest unit on each axis [tiles][32]
+    int sort_cap = 0;          // instances up to this many points are reordered (a power of two)
     float *d_P = nullptr;
     int *d_count = nullptr;
     uint8_t *d_core = nullptr;
@@ -221,8 +323,8 @@ struct BatchState {
     int *h_istats = nullptr;
     unsigned *h_status = nullptr;
     cudaGraphExec_t graph = nullptr;
-    int graph_ch = -1, graph_bps = -1, graph_stats = -1;
-    int ch = 16, bps = 8;
+    int graph_ch = -1, graph_bps = -1, graph_rm = -1, graph_stats = -1;
+    int ch = 16, bps = 8, rm = 4;  // column tiles per work item, blocks per SM, rows per thread (tile of 16 rm rows)
     bool tuned = false;
     PhaseMarks marks;  // timing off
 };
@@ -244,11 +346,13 @@ namespace {
 size_t al256(size_t v) { return (v + 255) / 256 * 256; }
 
 // (Re)allocates the batch workspace for at least these sizes.
-int batch_reserve(BatchState *b, int count, int64_t points, int64_t pfloats) {
-    if (count <= b->cap_count && points <= b->cap_points && pfloats <= b->cap_pfloats) return DBSCAN_OK;
+int batch_reserve(BatchState *b, int count, int64_t points, int64_t pfloats, int64_t tiles) {
+    if (count <= b->cap_count && points <= b->cap_points && pfloats <= b->cap_pfloats && tiles <= b->cap_tiles)
+        return DBSCAN_OK;
     const int nc = std::max(count, b->cap_count);
     const int64_t np = std::max<int64_t>(std::max(points, b->cap_points), 1);
     const int64_t nf = std::max<int64_t>(std::max(pfloats, b->cap_pfloats), 1);
+    const int64_t nt = std::max<int64_t>(std::max(tiles, b->cap_tiles), 1);
     const int64_t part = np / 2048 + 4;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -260,7 +364,7 @@ int batch_reserve(BatchState *b, int count, int64_t points, int64_t pfloats) {
                  o_P = take(4 * nf), o_count = take(4 * np), o_core = take(np), o_parent = take(4 * np),
                  o_border = take(4 * np), o_flags = take(4 * np), o_scan = take(4 * (np + 1)),
                  o_part = take(4 * part), o_work = take(4 * 8), o_status = take(16), o_istats = take(16 * nc),
-                 o_ev = take(24 * (size_t)nc);
+                 o_ev = take(24 * (size_t)nc), o_perm = take(4 * np), o_tbox = take(128 * (size_t)nt);
     if (b->graph) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
@@ -276,7 +380,7 @@ int batch_reserve(BatchState *b, int count, int64_t points, int64_t pfloats) {
     if (cudaMalloc(&b->dev, off) != cudaSuccess) {
         cudaGetLastError();
         b->cap_count = 0;
-        b->cap_points = b->cap_pfloats = 0;
+        b->cap_points = b->cap_pfloats = b->cap_tiles = 0;
         return DBSCAN_ERR_OOM;
     }
     if (cudaMallocHost(&b->h_table, sizeof(BInst) * nc) != cudaSuccess ||
@@ -290,6 +394,8 @@ int batch_reserve(BatchState *b, int count, int64_t points, int64_t pfloats) {
     b->d_table = reinterpret_cast<BInst *>(base + o_table);
     b->d_hdr = reinterpret_cast<BHdr *>(base + o_hdr);
     b->d_pinst = reinterpret_cast<int *>(base + o_pinst);
+    b->d_perm = reinterpret_cast<int *>(base + o_perm);
+    b->d_tbox = reinterpret_cast<float *>(base + o_tbox);
     b->d_P = reinterpret_cast<float *>(base + o_P);
     b->d_count = reinterpret_cast<int *>(base + o_count);
     b->d_core = reinterpret_cast<uint8_t *>(base + o_core);
@@ -306,13 +412,17 @@ int batch_reserve(BatchState *b, int count, int64_t points, int64_t pfloats) {
     b->cap_count = nc;
     b->cap_points = np;
     b->cap_pfloats = nf;
+    b->cap_tiles = nt;
     if (cudaMemset(b->d_status, 0, 16) != cudaSuccess) return DBSCAN_ERR_CUDA;
     return DBSCAN_OK;
 }
 
-// Host table for chunk size ch; returns total work items or -1 on a bad instance.
-int64_t build_table(const dbscan_instance *inst, int count, int ch, BInst *t, int64_t *points, int64_t *pfloats) {
-    int64_t base = 0, poff = 0, items = 0;
+// Host table for chunk size ch and row tiles of 16 * rm points; returns the
+// total work items.  boxes[lv] counts the tile boxes of 32 << lv rows.
+int64_t build_table(const dbscan_instance *inst, int count, int ch, int rm, BInst *t, int64_t *points,
+                    int64_t *pfloats, int64_t boxes[3], int64_t *max_n) {
+    int64_t base = 0, poff = 0, items = 0, mx = 0;
+    boxes[0] = boxes[1] = boxes[2] = 0;
     for (int i = 0; i < count; ++i) {
         const dbscan_instance &in = inst[i];
         BInst &I = t[i];
@@ -330,20 +440,39 @@ int64_t build_table(const dbscan_instance *inst, int count, int ch, BInst *t, in
         I.min_pts = in.min_pts;
         I.base = (int)base;
         I.poff = poff;
-        I.ntiles = (int)((in.n + BM - 1) / BM);
-        I.nchunks = (I.ntiles + ch - 1) / ch;
+        I.ntiles = (int)((in.n + 16 * rm - 1) / (16 * rm));
+        I.ctiles = (int)((in.n + BN - 1) / BN);
+        I.nchunks = (I.ctiles + ch - 1) / ch;
         I.item0 = (int)items;
+        for (int lv = 0; lv < 3; ++lv) {
+            I.box0[lv] = (int)boxes[lv];
+            boxes[lv] += (in.n + (32 << lv) - 1) / (32 << lv);
+        }
         I.pad = 0;
         base += in.n;
         poff += (in.n * I.dp + 3) / 4 * 4;  // 16-byte aligned rows of every instance (vector tile loads)
         items += (int64_t)I.ntiles * I.nchunks;
+        mx = std::max<int64_t>(mx, in.n);
     }
     *points = base;
     *pfloats = poff;
+    *max_n = mx;
     return items;
 }
 
-cudaError_t enqueue_batch(BatchState *b, int label_mode, bool stats, int ch, int bps, cudaStream_t st,
+template <int PASS>
+void launch_batch_pass(BatchState *b, int rm, int grid, int ch, int *work, bool stats, cudaStream_t st) {
+    unsigned long long *ev = stats ? b->d_ev : nullptr;
+#define DB_BATCH_PASS(R)                                                                                            \
+    batch_pass_kernel<PASS, R><<<grid, NT, 0, st>>>(b->d_table, b->d_hdr, ch, work, b->d_P, b->d_perm, b->d_tbox,  \
+                                                    b->d_count, b->d_core, b->d_parent, b->d_border, b->d_status, ev)
+    if (rm == 2) DB_BATCH_PASS(2);
+    else if (rm == 8) DB_BATCH_PASS(8);
+    else DB_BATCH_PASS(4);
+#undef DB_BATCH_PASS
+}
+
+cudaError_t enqueue_batch(BatchState *b, int label_mode, bool stats, int ch, int bps, int rm, cudaStream_t st,
                           PhaseMarks *pm = nullptr) {
     PhaseMarks off;
     if (!pm) pm = &off;
@@ -359,22 +488,20 @@ cudaError_t enqueue_batch(BatchState *b, int label_mode, bool stats, int ch, int
     if ((e = cudaMemsetAsync(b->d_count, 0, 4 * (size_t)b->cap_points, st))) return e;
     if (stats && (e = cudaMemsetAsync(b->d_istats, 0, 16 * (size_t)b->cap_count, st))) return e;
     if (stats && (e = cudaMemsetAsync(b->d_ev, 0, 24 * (size_t)b->cap_count, st))) return e;
-    batch_prep_kernel<<<egrid, 256, 0, st>>>(b->d_table, b->d_hdr, b->d_pinst, b->d_P, b->d_status);
+    batch_sortpack_kernel<<<sms * 2, 1024, sizeof(unsigned long long) * std::max(b->sort_cap, 2), st>>>(
+        b->d_table, b->d_hdr, b->sort_cap, b->d_pinst, b->d_perm, b->d_P, b->d_tbox, b->d_status);
     pm->kernel("batch_prep", st);
-    batch_pass_kernel<PASS_COUNT><<<pgrid, NT, 0, st>>>(b->d_table, b->d_hdr, ch, b->d_work + 0, b->d_P, b->d_count,
-                                                        b->d_core, b->d_parent, b->d_border, b->d_status, stats ? b->d_ev : nullptr);
+    launch_batch_pass<PASS_COUNT>(b, rm, pgrid, ch, b->d_work + 0, stats, st);
     pm->kernel("batch_count", st);
     batch_core_init_kernel<<<egrid, 256, 0, st>>>(b->d_table, b->d_hdr, b->d_pinst, b->d_count, b->d_core,
                                                   b->d_parent, b->d_border);
     pm->kernel("batch_core_init", st);
-    batch_pass_kernel<PASS_UNION><<<pgrid, NT, 0, st>>>(b->d_table, b->d_hdr, ch, b->d_work + 1, b->d_P, b->d_count,
-                                                        b->d_core, b->d_parent, b->d_border, b->d_status, stats ? b->d_ev : nullptr);
+    launch_batch_pass<PASS_UNION>(b, rm, pgrid, ch, b->d_work + 1, stats, st);
     pm->kernel("batch_union", st);
-    batch_pass_kernel<PASS_BORDER><<<pgrid, NT, 0, st>>>(b->d_table, b->d_hdr, ch, b->d_work + 2, b->d_P,
-                                                         b->d_count, b->d_core, b->d_parent, b->d_border, b->d_status,
-                                                         stats ? b->d_ev : nullptr);
+    launch_batch_pass<PASS_BORDER>(b, rm, pgrid, ch, b->d_work + 2, stats, st);
     pm->kernel("batch_border", st);
-    batch_label_kernel<<<egrid, 256, 0, st>>>(b->d_table, b->d_hdr, b->d_pinst, b->d_core, b->d_parent, b->d_border,
+    batch_label_kernel<<<egrid, 256, 0, st>>>(b->d_table, b->d_hdr, b->d_pinst, b->d_perm, b->d_core, b->d_parent,
+                                              b->d_border,
                                               b->d_flags, stats ? b->d_istats : nullptr);
     pm->kernel("batch_label", st);
     if ((e = cudaGetLastError())) return e;
@@ -397,8 +524,8 @@ cudaError_t enqueue_batch(BatchState *b, int label_mode, bool stats, int ch, int
 // The whole sequence as one CUDA graph (rebuilt when capacities or the tuned
 // configuration change).
 int batch_graph_launch(BatchState *b, int label_mode, bool stats, cudaStream_t st) {
-    if (!b->graph || b->graph_ch != b->ch || b->graph_bps != b->bps || b->graph_stats != (int)stats ||
-        b->graph_ch < 0) {
+    if (!b->graph || b->graph_ch != b->ch || b->graph_bps != b->bps || b->graph_rm != b->rm ||
+        b->graph_stats != (int)stats || b->graph_ch < 0) {
         if (b->graph) {
             cudaGraphExecDestroy(b->graph);
             b->graph = nullptr;
@@ -407,7 +534,7 @@ int batch_graph_launch(BatchState *b, int label_mode, bool stats, cudaStream_t s
         if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return DBSCAN_ERR_CUDA;
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        if (!e) e = enqueue_batch(b, label_mode, stats, b->ch, b->bps, cs);
+        if (!e) e = enqueue_batch(b, label_mode, stats, b->ch, b->bps, b->rm, cs);
         cudaError_t e2 = cudaStreamEndCapture(cs, &g);
         cudaStreamDestroy(cs);
         if (e || e2 || !g) {
@@ -424,6 +551,7 @@ int batch_graph_launch(BatchState *b, int label_mode, bool stats, cudaStream_t s
         }
         b->graph_ch = b->ch;
         b->graph_bps = b->bps;
+        b->graph_rm = b->rm;
         b->graph_stats = (int)stats;
     }
     return cudaGraphLaunch(b->graph, st) == cudaSuccess ? DBSCAN_OK : DBSCAN_ERR_CUDA;
@@ -447,8 +575,8 @@ extern "C" int dbscan_batch(dbscan_plan *plan, const dbscan_instance *inst, int3
     // smallest chunk gives the most items
     int64_t items = 0;
     for (int i = 0; i < count; ++i) {
-        const int64_t tiles = (inst[i].n + 63) / 64;
-        items += tiles * ((tiles + kCH[0] - 1) / kCH[0]);
+        const int64_t rows = (inst[i].n + 31) / 32, cols = (inst[i].n + 63) / 64;  // the smallest row tile
+        items += rows * ((cols + kCH[0] - 1) / kCH[0]);
     }
     if (items > INT32_MAX) return DBSCAN_ERR_UNSUPPORTED;
     int cur = -1;
@@ -462,34 +590,51 @@ extern "C" int dbscan_batch(dbscan_plan *plan, const dbscan_instance *inst, int3
 
     // Sizes for the largest chunk count (smallest CH) so every candidate fits.
     std::vector<BInst> tmp(count);
-    int64_t points = 0, pfloats = 0;
-    build_table(inst, count, kCH[0], tmp.data(), &points, &pfloats);
-    int s = batch_reserve(b, count, points, pfloats);
+    int64_t points = 0, pfloats = 0, boxes[3] = {0, 0, 0}, max_n = 0;
+    build_table(inst, count, kCH[0], kRM[0], tmp.data(), &points, &pfloats, boxes, &max_n);
+    int s = batch_reserve(b, count, points, pfloats, boxes[0] + boxes[1] + boxes[2]);
     if (s) return s;
+    // Instances up to kSortMax points are put in Z-order; the sort's shared
+    // memory is sized for the largest of them.
+    int sort_cap = 2;
+    while (sort_cap < std::min<int64_t>(max_n, kSortMax)) sort_cap <<= 1;
+    if (sort_cap != b->sort_cap && b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    b->sort_cap = sort_cap;
+    if (sizeof(unsigned long long) * sort_cap > 48 * 1024 &&
+        cudaFuncSetAttribute(batch_sortpack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(unsigned long long) * sort_cap)) != cudaSuccess)
+        return DBSCAN_ERR_CUDA;
 
-    auto prepare = [&](int ch) {
-        int64_t pts, pf;
-        const int64_t items = build_table(inst, count, ch, b->h_table, &pts, &pf);
+    auto prepare = [&](int ch, int rm) {
+        int64_t pts, pf, bx[3], mn;
+        const int64_t items = build_table(inst, count, ch, rm, b->h_table, &pts, &pf, bx, &mn);
         for (int i = count; i < b->cap_count; ++i) std::memset(&b->h_table[i], 0, sizeof(BInst));
         b->h_hdr->count = count;
         b->h_hdr->total_points = (int)pts;
         b->h_hdr->total_items = (int)std::min<int64_t>(items, INT32_MAX);
-        b->h_hdr->pad = 0;
+        b->h_hdr->box_level0[0] = 0;
+        b->h_hdr->box_level0[1] = (int)bx[0];
+        b->h_hdr->box_level0[2] = (int)(bx[0] + bx[1]);
+        b->h_hdr->pad[0] = b->h_hdr->pad[1] = 0;
     };
 
     if (!b->tuned) {
-        // Autotune on this batch: every (CH, blocks per SM) candidate, best of 2 runs.
+        // Autotune on this batch: every (row tile, CH, blocks per SM) candidate, best of 2 runs.
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         float best = 1e30f;
+        for (int rm : kRM)
         for (int ch : kCH)
             for (int bps : kBPS) {
-                prepare(ch);
+                prepare(ch, rm);
                 float tbest = 1e30f;
                 for (int rep = 0; rep < 2; ++rep) {
                     cudaEventRecord(e0, st);
-                    if (enqueue_batch(b, label_mode, false, ch, bps, st)) {
+                    if (enqueue_batch(b, label_mode, false, ch, bps, rm, st)) {
                         cudaEventDestroy(e0);
                         cudaEventDestroy(e1);
                         return DBSCAN_ERR_CUDA;
@@ -504,16 +649,17 @@ extern "C" int dbscan_batch(dbscan_plan *plan, const dbscan_instance *inst, int3
                     best = tbest;
                     b->ch = ch;
                     b->bps = bps;
+                    b->rm = rm;
                 }
             }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         b->tuned = true;
     }
-    prepare(b->ch);
+    prepare(b->ch, b->rm);
     if (plan->opts.profile) {  // per-kernel events: run the sequence uncaptured
         plan->marks.begin(st);
-        if (enqueue_batch(b, label_mode, stats, b->ch, b->bps, st, &plan->marks)) return DBSCAN_ERR_CUDA;
+        if (enqueue_batch(b, label_mode, stats, b->ch, b->bps, b->rm, st, &plan->marks)) return DBSCAN_ERR_CUDA;
     } else {
         s = batch_graph_launch(b, label_mode, stats, st);
         if (s) return s;
@@ -554,5 +700,13 @@ extern "C" int dbscan_batch_config(dbscan_plan *plan, int32_t *chunk_tiles, int3
     if (!plan->batch || !plan->batch->tuned) return DBSCAN_ERR_NOT_FOUND;
     if (chunk_tiles) *chunk_tiles = plan->batch->ch;
     if (blocks_per_sm) *blocks_per_sm = plan->batch->bps;
+    return DBSCAN_OK;
+}
+
+extern "C" int dbscan_batch_tile(dbscan_plan *plan, int32_t *tile_rows, int32_t *tile_cols) {
+    if (!plan) return DBSCAN_ERR_ARG;
+    if (!plan->batch || !plan->batch->tuned) return DBSCAN_ERR_NOT_FOUND;
+    if (tile_rows) *tile_rows = 16 * plan->batch->rm;
+    if (tile_cols) *tile_cols = BN;
     return DBSCAN_OK;
 }

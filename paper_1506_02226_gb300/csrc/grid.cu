@@ -34,9 +34,13 @@
 //   root     the union-find root of every cell with cores
 //   label    labels (a thread per point)
 // nbrs runs beside scatter, and border beside union, on the plan's second
-// stream: each pair is independent and latency-bound.
-// The pair kernels give one warp to one cell at a time and walk candidate
-// cells' points 32 lanes wide, four independent loads per lane in flight.
+// stream: each pair is independent and latency-bound.  Every kernel starts as
+// a programmatic dependent of the one before it in its stream, so its launch
+// overlaps that kernel's tail.
+// The count and border kernels give a thread to each grouped point, which
+// walks its cell's neighbour list (four entries and their ranges loaded at
+// once); the merge kernel gives a warp to one cell at a time, a lane to each
+// neighbouring cell, and searches a cell pair 32 lanes wide.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -63,7 +67,10 @@ __device__ __forceinline__ unsigned cell_key_of(const int *u, const GridGeom &g)
 }
 
 __global__ void grid_prep_kernel(const float *__restrict__ x, int n, GridGeom g, unsigned *hkey, int *hcount,
-                                 int *__restrict__ slot_of, float4 *__restrict__ pts4, unsigned *status) {
+                                 int *__restrict__ slot_of, float4 *__restrict__ pts4, int *__restrict__ parent,
+                                 unsigned *status) {
+    db::wait_prior_grid();  // started as a programmatic dependent
+    db::allow_next_grid();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const bool valid = i < n;
@@ -96,6 +103,7 @@ __global__ void grid_prep_kernel(const float *__restrict__ x, int n, GridGeom g,
         }
         slot = (int)h;
         slot_of[i] = slot;
+        parent[i] = i;  // every point starts as its own set; only cell representatives are ever linked
         const float f0 = (float)u[0], f1 = (float)u[1], f2 = (float)u[2];
         pts4[i] = make_float4(f0, f1, f2, -(f0 * f0 + f1 * f1 + f2 * f2));
     }
@@ -109,8 +117,10 @@ constexpr int CELLS_PER_THREAD = 4;
 __global__ void grid_cells_kernel(int H, int dense, const unsigned *__restrict__ hkey, const int *__restrict__ hcount,
                                   int2 *__restrict__ hpack, int *__restrict__ hcursor, int *__restrict__ cell_start,
                                   int *__restrict__ cell_count, unsigned *__restrict__ cell_key,
-                                  int *__restrict__ cell_rep, unsigned *__restrict__ occ,
-                                  unsigned long long *ctr0) {
+                                  int *__restrict__ cell_rep, unsigned long long *__restrict__ midkey,
+                                  unsigned *__restrict__ occ, unsigned long long *ctr0) {
+    db::wait_prior_grid();  // started as a programmatic dependent
+    db::allow_next_grid();
     __shared__ int wocc[32], wcnt[32];
     __shared__ unsigned long long base;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -150,6 +160,7 @@ __global__ void grid_cells_kernel(int H, int dense, const unsigned *__restrict__
             cell_count[cid] = cnt[k];
             cell_key[cid] = key;
             cell_rep[cid] = DB_NONE;
+            if (midkey) midkey[cid] = ~0ull;
             hpack[s] = make_int2((int)key, cid);
             hcursor[s] = start;
             if (occ) atomicOr(occ + (key >> 5), 1u << (key & 31u));
@@ -164,6 +175,8 @@ __global__ void grid_cells_kernel(int H, int dense, const unsigned *__restrict__
 __global__ void grid_scatter_kernel(int n, const int *__restrict__ slot_of, int *hcursor, const int2 *__restrict__ hpack,
                                     const float4 *__restrict__ pts4, float4 *__restrict__ spts, int *__restrict__ sidx,
                                     int *__restrict__ scell) {
+    db::wait_prior_grid();  // started as a programmatic dependent
+    db::allow_next_grid();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const bool valid = i < n;
@@ -182,12 +195,16 @@ __global__ void grid_scatter_kernel(int n, const int *__restrict__ slot_of, int 
 
 // Neighbour lists, a warp per cell: lane l looks up offsets l, l+32, l+64 and
 // l+96 (all loads independent), and the cells found are written compacted,
-// adjacent offsets first; ncnt[A] = (adjacent count << 16) | total count.
+// adjacent offsets first; ncnt[A] = (adjacent count << 16) | total count, and
+// cell_cand[A] = the points in the listed cells.
 // When the occupancy bitmap of all G^d cells fits its buffer (occ != null),
 // an empty neighbour costs one bit test and no hash probe.
 __global__ void grid_nbr_kernel(GridGeom g, const unsigned long long *ctr0, const unsigned *__restrict__ cell_key,
                                 const int2 *__restrict__ hpack, const unsigned *__restrict__ occ,
-                                int *__restrict__ nbr, int *__restrict__ ncnt) {
+                                const int *__restrict__ cell_count, int *__restrict__ nbr, int *__restrict__ ncnt,
+                                int *__restrict__ cell_cand) {
+    db::wait_prior_grid();  // started as a programmatic dependent
+    db::allow_next_grid();
     // Offsets go through shared memory into registers once: lanes indexing the
     // parameter array with different offsets would serialise on every read.
     __shared__ char4 soff[128];
@@ -260,7 +277,15 @@ __global__ void grid_nbr_kernel(GridGeom g, const unsigned long long *ctr0, cons
             nnear += __popc(hits & near_lanes);
             nn += __popc(hits);
         }
-        if (lane == 0) ncnt[A] = (nnear << 16) | nn;
+        // points in the listed cells: the candidates of each point of A
+        int tc = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) tc += res[u] >= 0 ? cell_count[res[u]] : 0;
+        tc = (int)__reduce_add_sync(FULL, (unsigned)tc);
+        if (lane == 0) {
+            ncnt[A] = (nnear << 16) | nn;
+            cell_cand[A] = tc;
+        }
     }
 }
 
@@ -275,11 +300,32 @@ __device__ __forceinline__ bool is_nbr(float cp, float px2, float py2, float pz2
     return acc >= 1.f;
 }
 
-// ---- warp-cooperative candidate scans -------------------------------------
-// A warp owns one cell A at a time.  The neighbour list of A is read 32
-// entries at a time: lane l holds (start, size) of one neighbour cell and an
-// inclusive prefix of the sizes, so the candidates of those cells form one
-// flattened range that the 32 lanes walk together, 32 candidates per step.
+struct PairArgs {
+    GridGeom g;
+    const unsigned long long *ctr0;
+    int n;
+    const float4 *spts;
+    const int *sidx;
+    const int *scell;  // cell of each grouped position
+    const int *cell_start, *cell_count, *cell_rep;
+    const unsigned long long *cell_mid;  // per cell: (squared distance to the centre << 32) | packed point
+    const unsigned *cell_key;
+    const int *nbr;   // neighbour cell lists, row stride g.noff
+    const int *ncnt;  // (adjacent count << 16) | count
+    const int *cell_cand;  // points in the cells of each neighbour list
+    unsigned long long *ev;  // pair tests evaluated: [0] count, [1] merge, [2] border, [3] outer-ring merge
+};
+
+// A point whose neighbour cells hold at most this many points walks them in
+// its own thread; the points of a cell with more are walked by the whole warp,
+// 32 candidates a step (a cell next to a tight blob can hold thousands).
+constexpr int kThreadWalkMax = 96;
+
+// ---- warp-cooperative candidate walk ---------------------------------------
+// The neighbour list of a cell is read 32 entries at a time: lane l holds
+// (start, size) of one neighbour cell and an inclusive prefix of the sizes, so
+// the candidates of those cells form one flattened range that the 32 lanes
+// walk together.
 
 __device__ __forceinline__ int warp_incl_scan(int v) {
     const int lane = threadIdx.x & 31;
@@ -291,201 +337,173 @@ __device__ __forceinline__ int warp_incl_scan(int v) {
     return v;
 }
 
-__device__ __forceinline__ int warp_min(int v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(FULL, v, o));
-    return v;
-}
-
-// Position of flattened candidate j: smallest lane k with incl[k] > j (5-step
-// binary search over the lanes' prefixes), then start[k] + (j - exclusive[k]).
-// All 32 lanes must call it; the result is meaningless when j >= total.
-__device__ __forceinline__ int locate(int j, int incl, int c, int s) {
+// Lane k holding flattened candidate j: the smallest lane with incl[k] > j (a
+// 5-step binary search over the lanes' prefixes); its position is then
+// start[k] + (j - exclusive[k]).  All 32 lanes must call it; the result is
+// meaningless when j >= total.
+__device__ __forceinline__ int locate_lane(int j, int incl) {
     int k = 0;
 #pragma unroll
     for (int step = 16; step >= 1; step >>= 1)
         if (__shfl_sync(FULL, incl, k + step - 1) <= j) k += step;
-    k &= 31;
-    const int ik = __shfl_sync(FULL, incl, k), ck = __shfl_sync(FULL, c, k), sk = __shfl_sync(FULL, s, k);
-    return sk + (j - (ik - ck));
+    return k & 31;
 }
 
-struct PairArgs {
-    GridGeom g;
-    const unsigned long long *ctr0;
-    const float4 *spts;
-    const int *sidx;
-    const int *cell_start, *cell_count, *cell_rep;
-    const float4 *cell_mid;
-    const unsigned *cell_key;
-    const int *nbr;   // neighbour cell lists, row stride g.noff
-    const int *ncnt;  // (adjacent count << 16) | count
-    unsigned long long *ev;  // pair tests evaluated: [0] count, [1] merge, [2] border, [3] outer-ring merge
-};
+// A point of the grid as {u0, u1, u2, -|u|^2} from its packed form
+// u0 | u1 << 10 | u2 << 20 (low 30 bits of a cell_mid entry).
+__device__ __forceinline__ float4 unpack_point(unsigned long long key) {
+    const unsigned v = (unsigned)key;
+    const float x = (float)(v & 1023u), y = (float)((v >> 10) & 1023u), z = (float)((v >> 20) & 1023u);
+    return make_float4(x, y, z, -(x * x + y * y + z * z));
+}
 
-// Count pass (Section IV-B, fused pair test + count).  Per cell A:
-//   |A| >= min_pts and no exact counts: every point is core, no pair test;
-//   |A| >= 32 with exact counts: one lane per point, candidates broadcast;
-//   otherwise (|A| < 32): the warp walks the flattened candidates, 128 per
-//   step with four independent loads per lane, and tests each step against
-//   every point of A that is still below min_pts (all of them with exact
-//   counts).
-// Then the smallest core index of A goes to cell_rep[A], and every core point
-// of A is hung under it in the union-find forest (cells are cliques); other
-// points are their own parent.  cell_mid[A] gets a core point of A near its
-// centre (among its first 128 points), which the merge pass tries first.
-template <int D>
-__global__ void __launch_bounds__(256, 6) grid_count_kernel(PairArgs a, int min_pts, int exact, uint8_t *score,
-                                                         int *cell_rep, float4 *cell_mid, int *parent,
-                                                         int *counts_out, uint8_t *core_out) {
+// Segmented minimum over a warp whose lanes hold consecutive grouped
+// positions (so equal cell ids are contiguous): afterwards the first lane of
+// each run of equal `cell` holds the minimum of `v` over its run.
+template <typename V>
+__device__ __forceinline__ V seg_min_down(V v, int cell) {
     const int lane = threadIdx.x & 31;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
-    const int ncells = (int)(*a.ctr0 >> 32);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const V y = __shfl_down_sync(FULL, v, o);
+        const int cy = __shfl_down_sync(FULL, cell, o);
+        if (lane + o < 32 && cy == cell) v = y < v ? y : v;
+    }
+    return v;
+}
+
+// Count pass (Section IV-B, fused pair test + count), a thread per grouped
+// position p in cell A.  The points of A are all neighbours (A is a clique),
+// so p starts at |A|; when |A| >= min_pts and no exact counts are asked for
+// p is core with no pair test.  Otherwise p tests the points of A's neighbour
+// cells, and stops once it has min_pts neighbours unless exact counts are
+// asked for: in its own thread when they are few (four list entries and their
+// ranges loaded at once), else together with the warp's other points of A,
+// the warp walking the candidates 128 a step with four independent loads per
+// lane.  Lanes of a warp hold consecutive positions, mostly of one cell, so
+// their loads coalesce.  Per cell, the smallest core index goes to
+// cell_rep[A] and the core point nearest A's centre (the merge pass tries it
+// first) to cell_mid[A], both by a segmented warp minimum and one atomic per
+// run of the cell's points in the warp.
+template <int D>
+__global__ void __launch_bounds__(256) grid_count_kernel(PairArgs a, int min_pts, int exact, uint8_t *score,
+                                                         int *cell_rep, unsigned long long *cell_mid,
+                                                         int *counts_out, uint8_t *core_out) {
+    db::wait_prior_grid();  // started as a programmatic dependent
+    db::allow_next_grid();
+    const int lane = threadIdx.x & 31;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = p < a.n;
     const int lim = exact ? INT_MAX : min_pts;
-    const int noff = a.g.noff;
-    // pair tests of each warp, kept in shared memory (no register held across the loops)
-    __shared__ unsigned wev[8];
-    unsigned &ev = wev[threadIdx.x >> 5];
-    if (lane == 0) ev = 0;
-    __syncwarp();
-    for (int A = warp; A < ncells; A += nwarps) {
-        const int sA = a.cell_start[A], cA = a.cell_count[A];
-        const int *row = a.nbr + (size_t)A * noff;
-        const int nn = a.ncnt[A] & 0xffff;
-        int minorig = DB_NONE;
-        if (cA >= lim) {
-            for (int i0 = lane; i0 < cA; i0 += 128) {
-                int o[4];
+    const int A = valid ? a.scell[p] : -1 - lane;  // no two invalid lanes share a cell
+    unsigned long long ev = 0;  // pair tests of this thread
+    int cnt = 0, o = DB_NONE;
+    bool heavy = false;
+    float4 pt = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) {
+        cnt = a.cell_count[A];
+        pt = a.spts[p];
+        o = a.sidx[p];
+    }
+    const float cp = a.g.Tp1 + pt.w, px2 = 2.f * pt.x, py2 = 2.f * pt.y, pz2 = 2.f * pt.z;
+    if (valid && cnt < lim) {
+        heavy = a.cell_cand[A] > kThreadWalkMax;
+        if (!heavy) {
+            const int *row = a.nbr + (size_t)A * a.g.noff;
+            const int nn = a.ncnt[A] & 0xffff;
+            for (int k0 = 0; k0 < nn && cnt < lim; k0 += 4) {
+                int s[4], e[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) o[u] = (i0 + 32 * u < cA) ? a.sidx[sA + i0 + 32 * u] : DB_NONE;
+                for (int u = 0; u < 4; ++u) s[u] = k0 + u < nn ? row[k0 + u] : -1;
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (i0 + 32 * u < cA) {
-                        score[sA + i0 + 32 * u] = 1;
-                        if (core_out) core_out[o[u]] = 1;
-                        minorig = min(minorig, o[u]);
-                    }
-            }
-        } else if (cA >= 32) {
-            for (int i0 = 0; i0 < cA; i0 += 32) {
-                const int i = i0 + lane;
-                const bool v = i < cA;
-                const int p = sA + (v ? i : 0);
-                const float4 pt = a.spts[p];
-                const float cp = a.g.Tp1 + pt.w, px2 = 2.f * pt.x, py2 = 2.f * pt.y, pz2 = 2.f * pt.z;
-                int cnt = cA;
-                for (int k = 0; k < nn; ++k) {
-                    if (__all_sync(FULL, cnt >= lim || !v)) break;
-                    const int B = row[k];
-                    const int s = a.cell_start[B], e = s + a.cell_count[B];
-                    for (int q = s; q < e; ++q) cnt += is_nbr<D>(cp, px2, py2, pz2, a.spts[q]);
-                    if (lane == 0) ev += (unsigned)(min(32, cA - i0) * (e - s));  // the lanes holding a point
+                for (int u = 0; u < 4; ++u) {
+                    const int B = s[u];
+                    s[u] = B >= 0 ? a.cell_start[B] : 0;
+                    e[u] = B >= 0 ? s[u] + a.cell_count[B] : 0;
                 }
-                if (v) {
-                    const bool core = cnt >= min_pts;
-                    const int o = a.sidx[p];
-                    score[p] = core;
-                    if (counts_out) counts_out[o] = cnt;
-                    if (core_out) core_out[o] = core;
-                    if (core) minorig = min(minorig, o);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    ev += (unsigned)(e[u] - s[u]);
+#pragma unroll 4
+                    for (int q = s[u]; q < e[u]; ++q) cnt += is_nbr<D>(cp, px2, py2, pz2, a.spts[q]);
                 }
             }
-        } else {
-            // |A| < 32: lane i owns point i of A.  Each chunk of candidates is
-            // loaded once and tested against every point still below the limit.
-            const bool mine = lane < cA;
-            const float4 pt = a.spts[sA + (mine ? lane : 0)];
-            const float cpm = a.g.Tp1 + pt.w, px2m = 2.f * pt.x, py2m = 2.f * pt.y, pz2m = 2.f * pt.z;
-            int cnt = cA;
-            unsigned pend = __ballot_sync(FULL, mine);  // cA < lim here
-            for (int k0 = 0; k0 < nn && pend; k0 += 32) {
-                const int B = (k0 + lane < nn) ? row[k0 + lane] : -1;
-                const int s = B >= 0 ? a.cell_start[B] : 0, c = B >= 0 ? a.cell_count[B] : 0;
-                const int incl = warp_incl_scan(c), total = __shfl_sync(FULL, incl, 31);
-                for (int base = 0; base < total && pend; base += 128) {
-                    float4 qq[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int j = base + 32 * u + lane;
-                        const int q = locate(j, incl, c, s);
-                        qq[u] = j < total ? a.spts[q] : make_float4(0.f, 0.f, 0.f, -1e30f);
-                    }
-                    if (lane == 0) ev += (unsigned)(__popc(pend) * min(128, total - base));
-                    for (unsigned m = pend; m; m &= m - 1) {
-                        const int i = __ffs(m) - 1;
-                        const float cp = __shfl_sync(FULL, cpm, i), px2 = __shfl_sync(FULL, px2m, i);
-                        const float py2 = D > 1 ? __shfl_sync(FULL, py2m, i) : 0.f;
-                        const float pz2 = D > 2 ? __shfl_sync(FULL, pz2m, i) : 0.f;
-                        int add = 0;
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) add += is_nbr<D>(cp, px2, py2, pz2, qq[u]);
-                        const int r = (int)__reduce_add_sync(FULL, (unsigned)add);
-                        if (lane == i) cnt += r;
-                    }
-                    pend = __ballot_sync(FULL, mine && cnt < lim);
-                }
-            }
-            if (mine) {
-                const int p = sA + lane;
-                const bool core = cnt >= min_pts;
-                const int o = a.sidx[p];
-                score[p] = core;
-                if (counts_out) counts_out[o] = cnt;
-                if (core_out) core_out[o] = core;
-                if (core) minorig = min(minorig, o);
-            }
-        }
-        minorig = warp_min(minorig);
-        if (lane == 0) cell_rep[A] = minorig;
-        __syncwarp();
-        // A's centre in doubled grid units, for the core point nearest to it
-        const unsigned key = a.cell_key[A];
-        const int G = a.g.G, cc = a.g.c;
-        const int cx2 = 2 * (int)(key % G) * cc + cc - 1, cy2 = 2 * (int)((key / G) % G) * cc + cc - 1,
-                  cz2 = 2 * (int)(key / ((unsigned)G * G)) * cc + cc - 1;
-        unsigned long long near = ~0ull;  // (squared distance to the centre << 32) | position
-        for (int i0 = lane; i0 < cA; i0 += 128) {
-            int o[4];
-            uint8_t sc[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const bool v = i0 + 32 * u < cA;
-                o[u] = v ? a.sidx[sA + i0 + 32 * u] : 0;
-                sc[u] = v ? score[sA + i0 + 32 * u] : 0;
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (i0 + 32 * u < cA) parent[o[u]] = sc[u] ? minorig : o[u];
-            if (i0 < 32) {  // among the first 128 points only
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (sc[u]) {
-                        const float4 q = a.spts[sA + i0 + 32 * u];
-                        const int dx = 2 * (int)q.x - cx2, dy = D > 1 ? 2 * (int)q.y - cy2 : 0,
-                                  dz = D > 2 ? 2 * (int)q.z - cz2 : 0;
-                        const unsigned long long k =
-                            ((unsigned long long)(unsigned)(dx * dx + dy * dy + dz * dz) << 32) | (unsigned)(i0 + 32 * u);
-                        near = k < near ? k : near;
-                    }
-            }
-        }
-        if (minorig != DB_NONE) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long y = __shfl_xor_sync(FULL, near, o);
-                near = y < near ? y : near;
-            }
-            if (lane == 0) cell_mid[A] = a.spts[sA + (int)(near & 0xffffffffull)];
         }
     }
-    __syncwarp();
-    db::block_sum_add(a.ev + 0, lane == 0 ? ev : 0u);
+    // cells with many candidates: the warp walks each one's candidates for its
+    // lanes of that cell still below the limit
+    unsigned hv = __ballot_sync(FULL, heavy);
+    while (hv) {
+        const int H = __shfl_sync(FULL, A, __ffs(hv) - 1);
+        const unsigned mine = __ballot_sync(FULL, heavy && A == H);
+        hv &= ~mine;
+        const int *row = a.nbr + (size_t)H * a.g.noff;
+        const int nn = a.ncnt[H] & 0xffff;
+        unsigned pend = mine;
+        for (int k0 = 0; k0 < nn && pend; k0 += 32) {
+            const int B = (k0 + lane < nn) ? row[k0 + lane] : -1;
+            const int s = B >= 0 ? a.cell_start[B] : 0, c = B >= 0 ? a.cell_count[B] : 0;
+            const int incl = warp_incl_scan(c), total = __shfl_sync(FULL, incl, 31);
+            for (int base = 0; base < total && pend; base += 128) {
+                float4 qq[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = base + 32 * u + lane;
+                    const int k = locate_lane(j, incl);
+                    const int ex = __shfl_sync(FULL, incl, k) - __shfl_sync(FULL, c, k);  // lane k's first j
+                    const int q = __shfl_sync(FULL, s, k) + (j - ex);
+                    qq[u] = j < total ? a.spts[q] : make_float4(0.f, 0.f, 0.f, -1e30f);
+                }
+                if (lane == 0) ev += (unsigned long long)__popc(pend) * (unsigned)min(128, total - base);
+                for (unsigned m = pend; m; m &= m - 1) {
+                    const int i = __ffs(m) - 1;
+                    const float cpi = __shfl_sync(FULL, cp, i), px2i = __shfl_sync(FULL, px2, i);
+                    const float py2i = D > 1 ? __shfl_sync(FULL, py2, i) : 0.f;
+                    const float pz2i = D > 2 ? __shfl_sync(FULL, pz2, i) : 0.f;
+                    int add = 0;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) add += is_nbr<D>(cpi, px2i, py2i, pz2i, qq[u]);
+                    const int r = (int)__reduce_add_sync(FULL, (unsigned)add);
+                    if (lane == i) cnt += r;
+                }
+                pend = __ballot_sync(FULL, ((mine >> lane) & 1u) && cnt < lim);
+            }
+        }
+    }
+    if (valid) {
+        const bool core = cnt >= min_pts;
+        score[p] = core;
+        if (counts_out) counts_out[o] = cnt;
+        if (core_out) core_out[o] = core;
+        if (!core) o = DB_NONE;
+    }
+    // the core point nearest A's centre, in doubled grid units (cell coordinate
+    // floor(u / c) from the exact float form of GridGeom.inv_c)
+    unsigned long long mid = ~0ull;
+    if (o != DB_NONE) {
+        const int c = a.g.c;
+        const int ux = (int)pt.x, uy = (int)pt.y, uz = (int)pt.z;
+        const int dx = 2 * ux - (2 * (int)((pt.x + 0.5f) * a.g.inv_c) * c + c - 1);
+        const int dy = D > 1 ? 2 * uy - (2 * (int)((pt.y + 0.5f) * a.g.inv_c) * c + c - 1) : 0;
+        const int dz = D > 2 ? 2 * uz - (2 * (int)((pt.z + 0.5f) * a.g.inv_c) * c + c - 1) : 0;
+        mid = ((unsigned long long)(unsigned)(dx * dx + dy * dy + dz * dz) << 32) |
+              (unsigned)(ux | (uy << 10) | (uz << 20));
+    }
+    o = seg_min_down(o, A);
+    mid = seg_min_down(mid, A);
+    const int Aprev = __shfl_up_sync(FULL, A, 1);
+    if (valid && (lane == 0 || Aprev != A) && o != DB_NONE) {
+        atomicMin(cell_rep + A, o);
+        atomicMin(cell_mid + A, mid);
+    }
+    db::block_sum_add(a.ev + 0, ev);
 }
 
 // Merge pass (Section IV-C).  The core points of one cell are already one set
-// (cells are cliques).  Lanes look at up to 32 neighbouring cells B of A at
-// once (the adjacent part of A's neighbour list in one launch, the outer ring
-// in a second; each cell pair from its smaller key).  In the adjacent launch,
+// (cells are cliques).  A warp takes one cell A at a time; its lanes look at
+// up to 32 neighbouring cells B of A at once (the adjacent part of A's
+// neighbour list in one launch, the outer ring in a second; each cell pair
+// from its smaller key).  In the adjacent launch,
 // a lane whose two central core points (cell_mid) are within eps unites the
 // two sets at once; for every other B with cores that is not yet in A's set,
 // the warp searches for one core pair within eps and unites the two sets at
@@ -496,6 +514,8 @@ template <int D>
 __global__ void __launch_bounds__(256) grid_union_kernel(PairArgs a, const uint8_t *__restrict__ score, int *parent,
                                                          unsigned *status, bool far_ring,
                                                          const int *__restrict__ croot) {
+    db::wait_prior_grid();  // started as a programmatic dependent
+    db::allow_next_grid();
     __shared__ float4 ybuf[8][128];
     __shared__ uint8_t ycore[8][128];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -503,27 +523,35 @@ __global__ void __launch_bounds__(256) grid_union_kernel(PairArgs a, const uint8
     const int ncells = (int)(*a.ctr0 >> 32);
     float4 *yb = ybuf[wib];
     uint8_t *yc = ycore[wib];
-    unsigned ev = 0;  // pair tests this lane accounts for (a warp sees far below 2^32 per launch)
+    unsigned long long ev = 0;  // pair tests this lane accounts for
+    const bool use_mid = !far_ring;
     for (int A = warp; A < ncells; A += nwarps) {
+        // A's entries in one round of independent loads (wasted on a cell without cores)
         const int repA = a.cell_rep[A];
-        if (repA == DB_NONE) continue;
         const unsigned keyA = a.cell_key[A];
         const int sA = a.cell_start[A], cA = a.cell_count[A];
-        const int *row = a.nbr + (size_t)A * a.g.noff;
         const int nc = a.ncnt[A];
-        const int k_begin = far_ring ? (nc >> 16) : 0, k_end = far_ring ? (nc & 0xffff) : (nc >> 16);
-        const bool use_mid = !far_ring;
-        const float4 mA = use_mid ? a.cell_mid[A] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const unsigned long long mkA = use_mid ? a.cell_mid[A] : 0ull;
         const int crA = croot ? croot[A] : -1;
+        if (repA == DB_NONE) continue;
+        const int *row = a.nbr + (size_t)A * a.g.noff;
+        const int k_begin = far_ring ? (nc >> 16) : 0, k_end = far_ring ? (nc & 0xffff) : (nc >> 16);
+        const float4 mA = unpack_point(mkA);
         const float cmA = a.g.Tp1 + mA.w, mx2 = 2.f * mA.x, my2 = 2.f * mA.y, mz2 = 2.f * mA.z;
         for (int k0 = k_begin; k0 < k_end; k0 += 32) {
             const int k = k0 + lane;
             const int B = k < k_end ? row[k] : -1;
-            const int repB = (B >= 0 && a.cell_key[B] > keyA) ? a.cell_rep[B] : DB_NONE;
-            const float4 mB = (use_mid && repB != DB_NONE) ? a.cell_mid[B] : make_float4(0.f, 0.f, 0.f, -1e30f);
+            // B's entries in one round of independent loads; each cell pair is
+            // examined from its smaller key
+            const unsigned keyB = B >= 0 ? a.cell_key[B] : 0u;
+            int repB = B >= 0 ? a.cell_rep[B] : DB_NONE;
+            const unsigned long long mkB = (use_mid && B >= 0) ? a.cell_mid[B] : 0ull;
+            const int crB = (croot && B >= 0) ? croot[B] : -2;
+            if (keyB <= keyA) repB = DB_NONE;
+            const float4 mB = repB != DB_NONE ? unpack_point(mkB) : make_float4(0.f, 0.f, 0.f, -1e30f);
             bool need = repB != DB_NONE;
             // cells whose snapshot roots agree are in one set already (sets only merge)
-            if (need && croot) need = croot[B] != crA;
+            if (need && croot) need = crB != crA;
             if (need) need = db::uf_find(parent, repA) != db::uf_find(parent, repB);
             // the two central core points first: a hit unites at once, lanes in parallel
             const bool hit = need && use_mid && is_nbr<D>(cmA, mx2, my2, mz2, mB);
@@ -584,77 +612,129 @@ __global__ void __launch_bounds__(256) grid_union_kernel(PairArgs a, const uint8
 }
 
 // Border pass: each non-core point takes its smallest-index core neighbour
-// (the reading used for points reachable from several clusters).  Only cells
-// with fewer than min_pts points hold non-core points.  The own cell's
-// representative is a neighbour (cliques); other cells are skipped when their
-// representative (their smallest core index) cannot beat the current best of
-// any point.  Candidates are walked 128 per step, four independent loads per
-// lane, and each step is tested against every non-core point of A.
+// (the reading used for points reachable from several clusters), a thread per
+// grouped position; core positions have nothing to do.  The own cell's
+// representative (its smallest core index) is a neighbour (cells are
+// cliques); a neighbour cell is walked only when its representative can beat
+// the current best, and a candidate is tested only when it is core with a
+// smaller index.  As in the count pass, a point with few candidates walks them
+// in its own thread, and the warp walks together for the points of a cell
+// with many.  bord[p] gets the cell of the chosen core point (DB_NONE for
+// noise): the point's label is that cell's root.
 template <int D>
-__global__ void __launch_bounds__(256) grid_border_kernel(PairArgs a, int min_pts, const uint8_t *__restrict__ score,
+__global__ void __launch_bounds__(256) grid_border_kernel(PairArgs a, const uint8_t *__restrict__ score,
                                                           int *__restrict__ bord) {
+    db::wait_prior_grid();  // started as a programmatic dependent
+    db::allow_next_grid();
     const int lane = threadIdx.x & 31;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
-    const int ncells = (int)(*a.ctr0 >> 32);
-    const int noff = a.g.noff;
-    unsigned ev = 0;  // pair tests this lane accounts for (a warp sees far below 2^32 per launch)
-    for (int A = warp; A < ncells; A += nwarps) {
-        const int sA = a.cell_start[A], cA = a.cell_count[A];
-        if (cA >= min_pts) continue;  // all core
-        const int repA = a.cell_rep[A];
-        const int *row = a.nbr + (size_t)A * noff;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = p < a.n;
+    const bool mine = valid && !score[p];
+    const int A = valid ? a.scell[p] : -1 - lane;
+    unsigned long long ev = 0;  // pair tests of this thread
+    int best = DB_NONE, bc = DB_NONE;
+    bool heavy = false;
+    float4 pt = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (mine) {
+        best = a.cell_rep[A];
+        bc = best != DB_NONE ? A : DB_NONE;
+        pt = a.spts[p];
+        heavy = a.cell_cand[A] > kThreadWalkMax;
+    }
+    const float cp = a.g.Tp1 + pt.w, px2 = 2.f * pt.x, py2 = 2.f * pt.y, pz2 = 2.f * pt.z;
+    if (mine && !heavy) {
+        const int *row = a.nbr + (size_t)A * a.g.noff;
         const int nn = a.ncnt[A] & 0xffff;
-        for (int i0 = 0; i0 < cA; i0 += 32) {
-            // lane i owns point i0 + i of A when it is not core
-            const int i = i0 + lane;
-            const bool mine = i < cA && !score[sA + i];
-            const unsigned pend = __ballot_sync(FULL, mine);
-            if (!pend) continue;
-            const float4 pt = a.spts[sA + (i < cA ? i : 0)];
-            const float cpm = a.g.Tp1 + pt.w, px2m = 2.f * pt.x, py2m = 2.f * pt.y, pz2m = 2.f * pt.z;
-            int b = repA;  // the own cell's smallest core index (cells are cliques)
-            for (int k0 = 0; k0 < nn; k0 += 32) {
-                const int B = (k0 + lane < nn) ? row[k0 + lane] : -1;
-                const int r = B >= 0 ? a.cell_rep[B] : DB_NONE;
-                const int s = B >= 0 ? a.cell_start[B] : 0;
-                int c = B >= 0 ? a.cell_count[B] : 0;
-                const int bmax = (int)__reduce_max_sync(FULL, mine ? (unsigned)b : 0u);
-                if (r >= bmax) c = 0;  // cannot beat any point's current best
-                const int incl = warp_incl_scan(c), total = __shfl_sync(FULL, incl, 31);
-                for (int base = 0; base < total; base += 128) {
-                    float4 qq[4];
-                    int qi[4];
+        for (int k0 = 0; k0 < nn; k0 += 4) {
+            int B[4], r[4], s[4], e[4];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int j = base + 32 * u + lane;
-                        const int q = locate(j, incl, c, s);
-                        const bool v = j < total;
-                        const uint8_t scq = v ? score[q] : 0;  // three independent loads
-                        const int qv = v ? a.sidx[q] : DB_NONE;
-                        qq[u] = v ? a.spts[q] : make_float4(0.f, 0.f, 0.f, -1e30f);
-                        qi[u] = scq ? qv : DB_NONE;
-                    }
-                    for (unsigned m = pend; m; m &= m - 1) {
-                        const int k = __ffs(m) - 1;
-                        const float cp = __shfl_sync(FULL, cpm, k), px2 = __shfl_sync(FULL, px2m, k);
-                        const float py2 = D > 1 ? __shfl_sync(FULL, py2m, k) : 0.f;
-                        const float pz2 = D > 2 ? __shfl_sync(FULL, pz2m, k) : 0.f;
-                        const int bk = __shfl_sync(FULL, b, k);
-                        int best = bk;
+            for (int u = 0; u < 4; ++u) B[u] = k0 + u < nn ? row[k0 + u] : -1;
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const bool better = qi[u] < best;  // else the pair needs no test
-                            ev += better;
-                            if (better && is_nbr<D>(cp, px2, py2, pz2, qq[u])) best = qi[u];
+            for (int u = 0; u < 4; ++u) {
+                r[u] = B[u] >= 0 ? a.cell_rep[B[u]] : DB_NONE;
+                s[u] = B[u] >= 0 ? a.cell_start[B[u]] : 0;
+                e[u] = B[u] >= 0 ? s[u] + a.cell_count[B[u]] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (r[u] >= best) continue;  // no core index of B can beat the current best
+                for (int q = s[u]; q < e[u]; ++q) {
+                    const uint8_t sc = score[q];  // three independent loads
+                    const int qi = a.sidx[q];
+                    const float4 pq = a.spts[q];
+                    if (sc && qi < best) {
+                        ++ev;
+                        if (is_nbr<D>(cp, px2, py2, pz2, pq)) {
+                            best = qi;
+                            bc = B[u];
                         }
-                        best = (int)__reduce_min_sync(FULL, (unsigned)best);
-                        if (lane == k) b = best;
                     }
                 }
             }
-            if (mine) bord[sA + i] = b;
         }
     }
+    unsigned hv = __ballot_sync(FULL, heavy);
+    while (hv) {
+        const int H = __shfl_sync(FULL, A, __ffs(hv) - 1);
+        const unsigned mineH = __ballot_sync(FULL, heavy && A == H);
+        hv &= ~mineH;
+        const bool inH = (mineH >> lane) & 1u;
+        const int *row = a.nbr + (size_t)H * a.g.noff;
+        const int nn = a.ncnt[H] & 0xffff;
+        for (int k0 = 0; k0 < nn; k0 += 32) {
+            const int B = (k0 + lane < nn) ? row[k0 + lane] : -1;
+            const int r = B >= 0 ? a.cell_rep[B] : DB_NONE;
+            const int s = B >= 0 ? a.cell_start[B] : 0;
+            int c = B >= 0 ? a.cell_count[B] : 0;
+            const int bmax = (int)__reduce_max_sync(FULL, inH ? (unsigned)best : 0u);
+            if (r >= bmax) c = 0;  // cannot beat any point's current best
+            const int incl = warp_incl_scan(c), total = __shfl_sync(FULL, incl, 31);
+            for (int base = 0; base < total; base += 128) {
+                float4 qq[4];
+                int qi[4], qc[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = base + 32 * u + lane;
+                    const int k = locate_lane(j, incl);
+                    const int ex = __shfl_sync(FULL, incl, k) - __shfl_sync(FULL, c, k);  // lane k's first j
+                    const int q = __shfl_sync(FULL, s, k) + (j - ex);
+                    qc[u] = __shfl_sync(FULL, B, k);
+                    const bool v = j < total;
+                    const uint8_t scq = v ? score[q] : 0;  // three independent loads
+                    const int qv = v ? a.sidx[q] : DB_NONE;
+                    qq[u] = v ? a.spts[q] : make_float4(0.f, 0.f, 0.f, -1e30f);
+                    qi[u] = scq ? qv : DB_NONE;
+                }
+                for (unsigned m = mineH; m; m &= m - 1) {
+                    const int i = __ffs(m) - 1;
+                    const float cpi = __shfl_sync(FULL, cp, i), px2i = __shfl_sync(FULL, px2, i);
+                    const float py2i = D > 1 ? __shfl_sync(FULL, py2, i) : 0.f;
+                    const float pz2i = D > 2 ? __shfl_sync(FULL, pz2, i) : 0.f;
+                    const int bi = __shfl_sync(FULL, best, i);
+                    int lb = bi, lc = DB_NONE;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const bool better = qi[u] < lb;  // else the pair needs no test
+                        ev += better;
+                        if (better && is_nbr<D>(cpi, px2i, py2i, pz2i, qq[u])) {
+                            lb = qi[u];
+                            lc = qc[u];
+                        }
+                    }
+                    const int nb = (int)__reduce_min_sync(FULL, (unsigned)lb);
+                    if (nb < bi) {  // warp-uniform: the one lane holding nb has its cell
+                        const int w = __ffs(__ballot_sync(FULL, lb == nb)) - 1;
+                        const int cw = __shfl_sync(FULL, lc, w);
+                        if (lane == i) {
+                            best = nb;
+                            bc = cw;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (mine) bord[p] = bc;
     db::block_sum_add(a.ev + 2, ev);
 }
 
@@ -663,6 +743,8 @@ __global__ void __launch_bounds__(256) grid_border_kernel(PairArgs a, int min_pt
 // With ctr == null it only takes a snapshot of the roots (for the outer ring).
 __global__ void grid_cell_root_kernel(const unsigned long long *ctr0, const int *__restrict__ cell_rep, int *parent,
                                       int *__restrict__ cell_root, unsigned long long *ctr) {
+    db::wait_prior_grid();  // started as a programmatic dependent
+    db::allow_next_grid();
     __shared__ int red[8];
     const int ncells = (int)(*ctr0 >> 32);
     int nr = 0;
@@ -687,12 +769,13 @@ __global__ void grid_cell_root_kernel(const unsigned long long *ctr0, const int 
 }
 
 // Labels, a thread per grouped point: core points take their cell's root (the
-// cluster's smallest core index), border points the root of their chosen core
-// neighbour, noise -1.  Also counts core / border / noise points.
+// cluster's smallest core index), border points the root of the cell of their
+// chosen core neighbour, noise -1.  Also counts core / border / noise points.
 __global__ void grid_label_kernel(int n, const int *__restrict__ sidx, const int *__restrict__ scell,
                                   const uint8_t *__restrict__ score, const int *__restrict__ cell_root,
-                                  const int *__restrict__ bord, int *parent, int *__restrict__ labels,
-                                  unsigned long long *ctr) {
+                                  const int *__restrict__ bord, int *__restrict__ labels, unsigned long long *ctr) {
+    db::wait_prior_grid();  // started as a programmatic dependent
+    db::allow_next_grid();
     __shared__ int red[3][8];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int nc = 0, nb = 0, nn = 0;
@@ -703,12 +786,12 @@ __global__ void grid_label_kernel(int n, const int *__restrict__ sidx, const int
             lab = cell_root[scell[p]];
             ++nc;
         } else {
-            const int b = bord[p];
-            if (b == DB_NONE) {
+            const int bc = bord[p];  // the cell of the chosen core neighbour
+            if (bc == DB_NONE) {
                 lab = -1;
                 ++nn;
             } else {
-                lab = db::uf_find(parent, b);
+                lab = cell_root[bc];
                 ++nb;
             }
         }
@@ -778,17 +861,19 @@ void join(const DbWork &w, cudaStream_t st, cudaStream_t s2, int k) {
 template <int D>
 cudaError_t grid_pair_passes(const DbWork &w, const GridGeom &g, int n, int min_pts, bool exact, int32_t *labels,
                              int32_t *counts_out, uint8_t *core_out, cudaStream_t st) {
-    PairArgs a{g,          w.ctr,      w.spts,     w.sidx, w.cell_start, w.cell_count,
-               w.cell_rep, w.cell_mid, w.cell_key, w.nbr,  w.ncnt,       w.ctr + DB_CTR_EVAL};
-    const int wgrid = 152 * 16;  // 8 warps per block, warps stride over the cells
-    grid_count_kernel<D><<<wgrid, 256, 0, st>>>(a, min_pts, exact ? 1 : 0, w.score, w.cell_rep, w.cell_mid,
-                                                w.parent, counts_out, core_out);
+    unsigned long long *mid = reinterpret_cast<unsigned long long *>(w.cell_mid);  // 8 of its 16 bytes per cell
+    PairArgs a{g,          w.ctr, n,          w.spts, w.sidx, w.scell,       w.cell_start, w.cell_count,
+               w.cell_rep, mid,   w.cell_key, w.nbr,  w.ncnt, w.cell_cand, w.ctr + DB_CTR_EVAL};
+    const int wgrid = 152 * 16;  // merge: 8 warps per block, warps stride over the cells
+    const int pgrid = (n + 255) / 256;  // count, border: a thread per grouped position
+    launch_dependent(grid_count_kernel<D>, pgrid, 256, st, a, min_pts, exact ? 1 : 0, w.score, w.cell_rep, mid,
+                     counts_out, core_out);
     w.marks->kernel("grid_count", st);
     // The border pass needs the core flags but not the merge: it runs beside it.
     cudaStream_t s2 = fork(w, st, 2);
-    grid_border_kernel<D><<<wgrid, 256, 0, s2>>>(a, min_pts, w.score, w.border);
+    launch_dependent(grid_border_kernel<D>, pgrid, 256, s2, a, w.score, w.border);
     w.marks->kernel("grid_border", s2);
-    grid_union_kernel<D><<<wgrid, 256, 0, st>>>(a, w.score, w.parent, w.status, false, nullptr);
+    launch_dependent(grid_union_kernel<D>, wgrid, 256, st, a, w.score, w.parent, w.status, false, nullptr);
     w.marks->kernel("grid_union_near", st);
     if (g.noff > g.nnear) {
         // With a wide outer ring (3-D: 98 offsets), the roots after the adjacent
@@ -796,19 +881,20 @@ cudaError_t grid_pair_passes(const DbWork &w, const GridGeom &g, int n, int min_
         // the cell pairs already joined without two finds each.
         const int *croot = nullptr;
         if (g.noff - g.nnear > 32) {
-            grid_cell_root_kernel<<<152 * 4, 256, 0, st>>>(w.ctr, w.cell_rep, w.parent, w.hcount, nullptr);
+            launch_dependent(grid_cell_root_kernel, 152 * 4, 256, st, w.ctr, w.cell_rep, w.parent, w.hcount,
+                             nullptr);
             w.marks->kernel("grid_root_snapshot", st);
             croot = w.hcount;
         }
-        grid_union_kernel<D><<<wgrid, 256, 0, st>>>(a, w.score, w.parent, w.status, true, croot);
+        launch_dependent(grid_union_kernel<D>, wgrid, 256, st, a, w.score, w.parent, w.status, true, croot);
         w.marks->kernel("grid_union_far", st);
     }
     join(w, st, s2, 3);
     // the hash cursors are free after the scatter: they hold the cell roots
-    grid_cell_root_kernel<<<152 * 4, 256, 0, st>>>(w.ctr, w.cell_rep, w.parent, w.hcursor, w.ctr);
+    launch_dependent(grid_cell_root_kernel, 152 * 4, 256, st, w.ctr, w.cell_rep, w.parent, w.hcursor, w.ctr);
     w.marks->kernel("grid_cell_root", st);
-    grid_label_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, w.sidx, w.scell, w.score, w.hcursor, w.border, w.parent,
-                                                       labels, w.ctr);
+    launch_dependent(grid_label_kernel, pgrid, 256, st, n, w.sidx, w.scell, w.score, w.hcursor, w.border, labels,
+                     w.ctr);
     w.marks->kernel("grid_label", st);
     return cudaGetLastError();
 }
@@ -827,6 +913,7 @@ bool grid_geometry(int32_t d, int64_t Tc, int64_t n, GridGeom *g) {
     g->G = (int32_t)((1024 + c - 1) / c);
     g->Tc = (int32_t)Tc;
     g->Tp1 = (float)(Tc + 1);
+    g->inv_c = (float)(1.0 / (double)c);
     int bits = 10;
     while ((int64_t(1) << bits) < 2 * n) ++bits;
     g->hbits = bits;
@@ -878,13 +965,15 @@ cudaError_t launch_grid_path(const DbWork &w, const GridGeom &g0, const float *x
     unsigned *occ = (!g.dense && occ_words <= w.occ_cap) ? w.occ : nullptr;
     if (occ && (e = cudaMemsetAsync(occ, 0, sizeof(unsigned) * occ_words, st))) return e;
     const int nb = (n + 255) / 256;
-    grid_prep_kernel<<<nb, 256, 0, st>>>(x, n, g, w.hkey, w.hcount, w.slot_of, w.pts4, w.status);
+    launch_dependent(grid_prep_kernel, nb, 256, st, x, n, g, w.hkey, w.hcount, w.slot_of, w.pts4, w.parent,
+                     w.status);
     w.marks->kernel("grid_prep", st);
-    if ((e = launch_grid_cells(w, g, occ, st))) return e;
+    if ((e = launch_grid_cells(w, g, occ, reinterpret_cast<unsigned long long *>(w.cell_mid), st))) return e;
     // The neighbour lists need the cell table but not the grouped points.
     cudaStream_t s2 = fork(w, st, 0);
     if ((e = launch_grid_nbrs(w, g, occ, s2))) return e;
-    grid_scatter_kernel<<<nb, 256, 0, st>>>(n, w.slot_of, w.hcursor, w.hpack, w.pts4, w.spts, w.sidx, w.scell);
+    launch_dependent(grid_scatter_kernel, nb, 256, st, n, w.slot_of, w.hcursor, w.hpack, w.pts4, w.spts, w.sidx,
+                     w.scell);
     w.marks->kernel("grid_scatter", st);
     join(w, st, s2, 1);
     if ((e = cudaGetLastError())) return e;
@@ -895,22 +984,24 @@ cudaError_t launch_grid_path(const DbWork &w, const GridGeom &g0, const float *x
     }
 }
 
-cudaError_t launch_grid_cells(const DbWork &w, const GridGeom &g, unsigned *occ, cudaStream_t st) {
+cudaError_t launch_grid_cells(const DbWork &w, const GridGeom &g, unsigned *occ, unsigned long long *midkey,
+                              cudaStream_t st) {
     int64_t H = int64_t(1) << g.hbits;
     if (g.dense) {
         H = 1;
         for (int k = 0; k < g.d; ++k) H *= g.G;
     }
     const int cells_per_block = 256 * CELLS_PER_THREAD;
-    grid_cells_kernel<<<(unsigned)((H + cells_per_block - 1) / cells_per_block), 256, 0, st>>>(
-        (int)H, g.dense, w.hkey, w.hcount, w.hpack, w.hcursor, w.cell_start, w.cell_count, w.cell_key, w.cell_rep,
-        occ, w.ctr);
+    launch_dependent(grid_cells_kernel, (unsigned)((H + cells_per_block - 1) / cells_per_block), 256, st, (int)H,
+                     g.dense, w.hkey, w.hcount, w.hpack, w.hcursor, w.cell_start, w.cell_count, w.cell_key,
+                     w.cell_rep, midkey, occ, w.ctr);
     w.marks->kernel("grid_cells", st);
     return cudaGetLastError();
 }
 
 cudaError_t launch_grid_nbrs(const DbWork &w, const GridGeom &g, const unsigned *occ, cudaStream_t st) {
-    grid_nbr_kernel<<<152 * 16, 256, 0, st>>>(g, w.ctr, w.cell_key, w.hpack, occ, w.nbr, w.ncnt);
+    launch_dependent(grid_nbr_kernel, 152 * 16, 256, st, g, w.ctr, w.cell_key, w.hpack, occ, w.cell_count, w.nbr,
+                     w.ncnt, w.cell_cand);
     w.marks->kernel("grid_nbrs", st);
     return cudaGetLastError();
 }

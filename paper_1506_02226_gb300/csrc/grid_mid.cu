@@ -503,6 +503,7 @@ bool mid_geometry(int32_t d, int64_t Tc, int64_t n, GridGeom *g) {
     g->G = (int32_t)G;
     g->Tc = (int32_t)Tc;
     g->Tp1 = (float)(Tc + 1);
+    g->inv_c = (float)(1.0 / (double)g->c);
     int bits = 10;
     while ((int64_t(1) << bits) < 2 * n) ++bits;
     g->hbits = bits;
@@ -535,7 +536,7 @@ cudaError_t launch_mid_grid_path(const DbWork &w, const GridGeom &g, const float
     const int nb = (n + 255) / 256;
     mid_prep_kernel<<<nb, 256, 0, st>>>(x, n, d, g, w.hkey, w.hcount, w.slot_of, w.status);
     w.marks->kernel("mid_prep", st);
-    if ((e = launch_grid_cells(w, g, occ, st))) return e;
+    if ((e = launch_grid_cells(w, g, occ, nullptr, st))) return e;
     return DP == 4 ? mid_passes<4>(w, g, x, n, d, min_pts, exact, labels, counts_out, core_out, occ, st)
                    : mid_passes<8>(w, g, x, n, d, min_pts, exact, labels, counts_out, core_out, occ, st);
 }

@@ -5,6 +5,8 @@
 // eps-neighbour of p iff D(p,q) = sum_k (u_pk - u_qk)^2 <= T.
 #pragma once
 
+#include <utility>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -126,6 +128,17 @@ __device__ __forceinline__ void block_sum_add(unsigned long long *dst, unsigned 
     }
 }
 
+// Programmatic dependent launch.  A kernel started with launch_dependent()
+// may be scheduled while the kernel before it in its stream still runs: it
+// calls wait_prior_grid() before touching memory, which returns once that
+// kernel has completed and its writes are visible (at once for a kernel
+// started the plain way).  allow_next_grid() lets the next such kernel of the
+// stream be scheduled early; it still waits for this one to complete.  A
+// chain of short dependent kernels then overlaps each launch with the tail of
+// the kernel before it.
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_next_grid() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -133,6 +146,23 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 }
 
 }  // namespace db
+
+// Starts kern on st as a programmatic dependent of the previous kernel in st
+// (kern must call db::wait_prior_grid() before its first memory access).
+template <typename... P, typename... A>
+inline cudaError_t launch_dependent(void (*kern)(P...), dim3 grid, dim3 block, cudaStream_t st, A &&...args) {
+    cudaLaunchAttribute at{};
+    at.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at.val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
+}
 
 // ---------------------------------------------------------------------------
 // Per-kernel timing: when on, a CUDA event is recorded on the launch stream
@@ -198,6 +228,7 @@ struct DbWork {
     uint32_t *cell_key;     // [cap_n]
     int32_t *nbr;           // neighbour cell lists, adjacent first [cap_n * noff_cap]
     int32_t *ncnt;          // (adjacent count << 16) | count [cap_n]
+    int32_t *cell_cand;     // points in the cells of each neighbour list [cap_n]
     int32_t noff_cap;
     // tensor-core path (max_d >= 16)
     int64_t tc_cap_pad;     // rows of each packed operand (cap_n rounded up to 256)
@@ -219,6 +250,7 @@ struct GridGeom {
     int32_t d, c, G, Tc, noff, nnear, hbits;
     int32_t dense;  // 1: cells indexed directly by key (slot = key, G^d slots), 0: hashed (2^hbits slots)
     float Tp1;
+    float inv_c;    // 1/c rounded to FP32: floor((u + 1/2) * inv_c) = floor(u / c) for 0 <= u < 2^11
     char4 off[124];
 };
 
@@ -246,7 +278,8 @@ cudaError_t launch_grid_candidates(const DbWork &w, const GridGeom &g, int64_t n
 // Structure kernels shared by the eps-grid and the projected grid (grid_mid.cu):
 // occupied slots -> cell table (ids, ranges, keys, occupancy bits), and the
 // neighbour-cell lists of g's offsets.
-cudaError_t launch_grid_cells(const DbWork &w, const GridGeom &g, unsigned *occ, cudaStream_t st);
+cudaError_t launch_grid_cells(const DbWork &w, const GridGeom &g, unsigned *occ, unsigned long long *midkey,
+                              cudaStream_t st);
 cudaError_t launch_grid_nbrs(const DbWork &w, const GridGeom &g, const unsigned *occ, cudaStream_t st);
 // Projected grid for 4 <= d <= 8 (grid_mid.cu): geometry (false when the
 // cells would be too coarse to prune) and the whole path.

@@ -58,6 +58,7 @@ def test_batch_matches_oracle(mode):
             assert st[k].n_clusters == len(set(want[want >= 0].tolist()))
         ch, bps = B.dbscan_batch_config(p.handle)
         assert ch > 0 and bps > 0
+        assert B.dbscan_batch_tile(p.handle) in ((32, 64), (64, 64), (128, 64))
 
 
 def test_batch_graph_reuse_and_growth():
