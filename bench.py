@@ -173,10 +173,10 @@ def grid_offsets(d: int, T: int):
 # source means the counters no longer describe the kernel, and the bench line
 # reports traffic null.
 NCU_TRAFFIC = {
-    ("lowd2", "grid_count"): (12901888, "paper_1506_02226_gb300/csrc/grid.cu", "1995cd7ef4f6"),
-    ("lowd2", "grid_union_near"): (10777856, "paper_1506_02226_gb300/csrc/grid.cu", "1995cd7ef4f6"),
-    ("lowd3", "grid_count"): (30640896, "paper_1506_02226_gb300/csrc/grid.cu", "1995cd7ef4f6"),
-    ("lowd3", "grid_union_near"): (24302336, "paper_1506_02226_gb300/csrc/grid.cu", "1995cd7ef4f6"),
+    ("lowd2", "grid_count"): (17419776, "paper_1506_02226_gb300/csrc/grid.cu", "faffd4840d06"),
+    ("lowd2", "grid_union_near"): (10742272, "paper_1506_02226_gb300/csrc/grid.cu", "faffd4840d06"),
+    ("lowd3", "grid_count"): (32878592, "paper_1506_02226_gb300/csrc/grid.cu", "faffd4840d06"),
+    ("lowd3", "grid_union_near"): (23241728, "paper_1506_02226_gb300/csrc/grid.cu", "faffd4840d06"),
 }
 
 
@@ -706,6 +706,7 @@ def run_batch(args, steps=None):
                    "autotuned": {"tile": [tile_rows, tile_cols], "chunk_tiles": ch, "blocks_per_sm": bps},
                    "l2": "flushed by a 256 MiB write before every timed step"},
         "pair_tests_per_step": pair_tests, "pair_tests_per_s": pair_tests / (ms * 1e-3),
+        "pair_tests_by_pass": {"count": int(pass_pairs[0]), "merge": int(pass_pairs[1]), "border": int(pass_pairs[2])},
         "all_pairs_per_step": pairs,
         "launch_loop": {"jobs_per_s": count / (statistics.mean(loop_ms) * 1e-3), "ms": statistics.mean(loop_ms),
                         "what": "the same instances, one dbscan_run per instance on one stream"},
