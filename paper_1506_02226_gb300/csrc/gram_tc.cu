@@ -38,8 +38,10 @@
 //
 // CTA roles (320 threads for the FP16 count and the verification, 576
 // otherwise; one CTA per SM, persistent over work items):
-//   warp 0      producer: bulk copies of A tiles (2 buffers) and B tiles
-//               (4-stage ring), completion via mbarrier transaction counts
+//   warp 0      producer: bulk copies of A tiles (2 buffers), B tiles (a ring
+//               of 5 stages, 2 for BF16, each freed by the MMA commit of its
+//               tile) and their metadata (a 6-stage ring, freed by the
+//               epilogue), completion via mbarrier transaction counts
 //   warp 1      TMEM owner (alloc/dealloc of 512 columns) and MMA issuer:
 //               K/16 tcgen05.mma (M=128, N=256, K=16) per tile into one of two
 //               256-column accumulators; tcgen05.commit signals the epilogue
@@ -65,6 +67,9 @@ namespace {
 
 constexpr int TM = 128, TN = 256;
 constexpr int FP16_BAND = 0;  // FP16 Gram products are exact (see above): no band
+// BF16 candidate filter: lowering of its threshold that covers the rounding
+// difference between the filter score and the rare path's score (below 16).
+constexpr float kBf16FilterSlack = 16.f;
 // BF16 band in units of w = 2G - |v_q|^2 for padded dimension K (see above).
 __host__ __device__ constexpr int bf16_band(int K) { return 16 * K; }
 
@@ -101,7 +106,7 @@ struct MetaBlock {
     float beta[TM];
     float rho[TM];
     int idx[TM];
-    int pad[TM];
+    float beta_f[TM];  // the candidate filter's column term: beta (FP16), beta - rho^2 rounded (BF16)
 };
 
 struct TcArgs {
@@ -333,17 +338,22 @@ __device__ __noinline__ int exact_sqdist(const int16_t *__restrict__ v16, int K,
 }
 
 // Shared memory of one CTA: KC stored operand columns per row (64 for FP16,
-// 128 for the two BF16 terms) and NS stages of B tiles (4 for FP16: 32 KB each;
-// 2 for BF16: 64 KB each).
-template <int KC, int NS>
+// 128 for the two BF16 terms), NS stages of B tiles (5 for FP16: 32 KB each;
+// 2 for BF16: 64 KB each) and NM stages of their metadata.  A B stage is free
+// again once its MMAs have completed; the epilogue holds only the tile's
+// metadata, in a ring of its own, so the operand ring runs up to NS tiles
+// ahead of the MMAs whatever the epilogue's pace.
+template <int KC, int NS, int NM>
 struct __align__(16) SmemT {
     static constexpr int NSTAGE = NS;
+    static constexpr int NMETA = NM;
     uint16_t A[2][TM * KC];          // 2 x 16 KB (FP16) or 2 x 32 KB (BF16)
     uint16_t B[NS][TN * KC];
     MetaBlock metaA[2];              // 2 x 2 KB
-    MetaBlock metaB[NS][2];          // NS x 4 KB
+    MetaBlock metaB[NM][2];          // NM x 4 KB
     uint64_t a_full[2], a_empty[2];
     uint64_t b_full[NS], b_empty[NS];
+    uint64_t m_empty[NM];            // metadata stage released by the epilogue warps of its tile
     uint64_t t_full[2], t_empty[2];
     uint64_t drain;                  // abort path: one more MMA commit, waited for by the issuer
     uint32_t tmem_base;
@@ -409,8 +419,8 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
     // Align by pointer arithmetic on the shared array (not through an integer),
     // so the compiler keeps shared-space loads, stores and atomics.
     const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
-    using Smem = SmemT<BF16 ? 128 : 64, BF16 ? 2 : 4>;
-    constexpr int NSTAGE = Smem::NSTAGE;
+    using Smem = SmemT<BF16 ? 128 : 64, BF16 ? 2 : 5, 6>;
+    constexpr int NSTAGE = Smem::NSTAGE, NMETA = Smem::NMETA;
     Smem &S = *reinterpret_cast<Smem *>(smem_raw + pad);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nR = *a.nR_ptr, nC = *a.nC_ptr;
@@ -429,8 +439,9 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
         }
         for (int i = 0; i < NSTAGE; ++i) {
             mbar_init(&S.b_full[i], 1);
-            mbar_init(&S.b_empty[i], 1 + TILE_WARPS);
+            mbar_init(&S.b_empty[i], 1);  // the MMA commit of the tile
         }
+        for (int i = 0; i < NMETA; ++i) mbar_init(&S.m_empty[i], TILE_WARPS);
         mbar_init(&S.drain, 1);
         S.abort_flag = 0;
         S.drain_failed = 0;
@@ -467,11 +478,14 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
                 bulk_g2s(&S.metaA[ab], a.metaR + rt, sizeof(MetaBlock), &S.a_full[ab]);
                 last_a[ab] = ia >> 1;
                 for (int ct = c0; ct < c1; ++ct, ++t) {
-                    const int s = t % NSTAGE;
-                    if (!TC_WAIT(w_prod, mbar_wait(&S.b_empty[s], ((t / NSTAGE) & 1) ^ 1, abort_flag, a.wait_ns))) break;
+                    const int s = t % NSTAGE, m = t % NMETA;
+                    if (!TC_WAIT(w_prod, mbar_wait(&S.b_empty[s], ((t / NSTAGE) & 1) ^ 1, abort_flag, a.wait_ns)) ||
+                        !TC_WAIT(w_prod, mbar_wait(&S.m_empty[m], ((t / NMETA) & 1) ^ 1, abort_flag, a.wait_ns)))
+                        break;
+                    // the metadata lands in its own ring, counted by the tile's b_full
                     mbar_arrive_expect_tx(&S.b_full[s], b_bytes + 2 * sizeof(MetaBlock));
                     bulk_g2s(S.B[s], a.opC + (size_t)ct * TN * KS, b_bytes, &S.b_full[s]);
-                    bulk_g2s(&S.metaB[s][0], a.metaC + 2 * ct, 2 * sizeof(MetaBlock), &S.b_full[s]);
+                    bulk_g2s(&S.metaB[m][0], a.metaC + 2 * ct, 2 * sizeof(MetaBlock), &S.b_full[s]);
                     last_b[s] = t / NSTAGE;
                 }
             }
@@ -587,7 +601,7 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
             int rootp = (PASS == TC_UNION && row_ok) ? db::ld_relaxed(a.parent + p) : -2;
             bool ok = true;
             for (int ct = c0; ct < c1; ++ct, ++t) {
-                const int s = t % NSTAGE, b = t & 1;
+                const int m = t % NMETA, b = t & 1;
                 if (EPI_GROUPS == 2 && b != (ew >> 2)) continue;  // the other group's tile
                 // warp-uniform outcome: the accumulator loads below are warp-collective
                 // the accumulator is usually ready: test once inline before the bounded wait
@@ -598,7 +612,7 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
                     break;
                 }
                 tc_fence_after();
-                const MetaBlock &mc = S.metaB[s][half];
+                const MetaBlock &mc = S.metaB[m][half];
                 int *colroot = S.colroot[b][half];
                 bool hints = false;  // union: colroot filled for this tile
                 // union: the parents of this tile's 128 column points, loaded now so
@@ -636,7 +650,7 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
                             }
                         }
                     };
-                    const float *b0 = S.metaB[s][0].beta, *b1 = S.metaB[s][1].beta;
+                    const float *b0 = S.metaB[m][0].beta, *b1 = S.metaB[m][1].beta;
                     tmem_ld32_nowait(tb, ga);
                     tmem_wait_ld_dep(ga);
                     tmem_ld32_nowait(tb + 32, gb);
@@ -732,24 +746,26 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
                         if (row_ok) cnt += (int)(((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7])));
                         continue;
                     }
-                    // Union / border / BF16: per pair one FFMA (two for BF16); the
-                    // maxima of the eight strided column groups (j mod 8) come from
-                    // the first three levels of an FMNMX tree.  Only groups whose
-                    // maximum can reach the threshold are rescanned.
-                    // Candidate score per pair: 2G - |v_q|^2 (+ rho_p rho_q for BF16);
-                    // a group needs its rare path when the maximum reaches alpha.
-                    // FP16 computes the exact negation |v_q|^2 - 2G two pairs per packed
-                    // FFMA (round-to-nearest is symmetric) and takes minus its minimum;
-                    // BF16 keeps scalar FFMAs, whose registers fit beside the
-                    // accumulator copy its exact recheck needs.
-                    const float thr = BF16 ? alpha : alpha - (float)FP16_BAND;
+                    // Union / border / BF16: one FFMA per pair; the maxima of the
+                    // eight strided column groups (j mod 8) come from the first
+                    // three levels of an FMNMX tree.  Only groups whose maximum can
+                    // reach the threshold are rescanned.
+                    // Candidate score per pair: 2G - beta_f, computed as the exact
+                    // negation beta_f - 2G two pairs per packed FFMA (round-to-nearest
+                    // is symmetric), minus its minimum.  FP16: beta_f = |v_q|^2.
+                    // BF16: beta_f = |v_q|^2 - rho^2 (rho is the same for every point),
+                    // so the score is the rare path's 2G - |v_q|^2 + rho_p rho_q up to
+                    // a few units of rounding (at most 2 per rounding at magnitudes
+                    // below 2^25, two roundings on each side); the threshold is lowered
+                    // by kBf16FilterSlack to cover them, and the rare path decides.
+                    const float thr = BF16 ? alpha - kBf16FilterSlack : alpha - (float)FP16_BAND;
                     float mx;
-                    if (!BF16) {
+                    {
                         float nv[GW];
                         const unsigned long long m2 = f2_pack(-2.f, -2.f);
 #pragma unroll
                         for (int j4 = 0; j4 < GW / 4; ++j4) {
-                            const float4 b4 = *reinterpret_cast<const float4 *>(&mc.beta[cb + 4 * j4]);
+                            const float4 b4 = *reinterpret_cast<const float4 *>(&mc.beta_f[cb + 4 * j4]);
                             const unsigned long long w01 =
                                 f2_fma(f2_pack(__uint_as_float(g[4 * j4 + 0]), __uint_as_float(g[4 * j4 + 1])), m2,
                                        f2_pack(b4.x, b4.y));
@@ -765,23 +781,6 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
                             for (int j = 0; j < w2; ++j) nv[j] = fminf(nv[j], nv[j + w2]);
                         mx = -fminf(fminf(fminf(nv[0], nv[1]), fminf(nv[2], nv[3])),
                                     fminf(fminf(nv[4], nv[5]), fminf(nv[6], nv[7])));
-                    } else {
-                        float wv[GW];
-#pragma unroll
-                        for (int j4 = 0; j4 < GW / 4; ++j4) {
-                            const float4 b4 = *reinterpret_cast<const float4 *>(&mc.beta[cb + 4 * j4]);
-                            const float4 r4 = *reinterpret_cast<const float4 *>(&mc.rho[cb + 4 * j4]);
-                            wv[4 * j4 + 0] = fmaf(rho_p, r4.x, fmaf(2.f, __uint_as_float(g[4 * j4 + 0]), -b4.x));
-                            wv[4 * j4 + 1] = fmaf(rho_p, r4.y, fmaf(2.f, __uint_as_float(g[4 * j4 + 1]), -b4.y));
-                            wv[4 * j4 + 2] = fmaf(rho_p, r4.z, fmaf(2.f, __uint_as_float(g[4 * j4 + 2]), -b4.z));
-                            wv[4 * j4 + 3] = fmaf(rho_p, r4.w, fmaf(2.f, __uint_as_float(g[4 * j4 + 3]), -b4.w));
-                        }
-#pragma unroll
-                        for (int w2 = GW / 2; w2 >= 8; w2 >>= 1)
-#pragma unroll
-                            for (int j = 0; j < w2; ++j) wv[j] = fmaxf(wv[j], wv[j + w2]);
-                        mx = fmaxf(fmaxf(fmaxf(wv[0], wv[1]), fmaxf(wv[2], wv[3])),
-                                   fmaxf(fmaxf(wv[4], wv[5]), fmaxf(wv[6], wv[7])));
                     }
                     // Border: the columns are core points in ascending index order,
                     // so a group whose first index is not below the best so far
@@ -862,7 +861,7 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
                 __syncwarp();
                 if (lane == 0) {
                     mbar_arrive(&S.t_empty[b]);
-                    mbar_arrive(&S.b_empty[s]);
+                    mbar_arrive(&S.m_empty[m]);
                 }
             }
             if (row_ok) {
@@ -993,7 +992,7 @@ __global__ void tc_pack_kernel(const int *__restrict__ list, const int *__restri
                 m.rho[r] = 0.f;
                 m.idx[r] = -1;
             }
-            m.pad[r] = 0;
+            m.beta_f[r] = valid ? (bf16 ? (float)nrm[p] - rho_c * rho_c : (float)nrm[p]) : 1e30f;
         }
     }
 }
@@ -1021,7 +1020,7 @@ __global__ void core_flags_kernel(int n, const uint8_t *__restrict__ core, int *
 
 template <bool BF16>
 size_t tc_smem_bytes() {
-    return sizeof(SmemT<BF16 ? 128 : 64, BF16 ? 2 : 4>) + 1024;
+    return sizeof(SmemT<BF16 ? 128 : 64, BF16 ? 2 : 5, 6>) + 1024;
 }
 
 template <int PASS, bool BF16>
