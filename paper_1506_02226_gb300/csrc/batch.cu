@@ -51,16 +51,6 @@ struct BHdr {  // device-side sizes of the current batch
     int pad[2];
 };
 
-__device__ __forceinline__ int find_inst_by_base(const BInst *__restrict__ t, int count, int g) {
-    int lo = 0, hi = count - 1;  // last instance with base <= g
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (t[mid].base <= g) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
 __device__ __forceinline__ int find_inst_by_item(const BInst *__restrict__ t, int count, int item) {
     int lo = 0, hi = count - 1;
     while (lo < hi) {
