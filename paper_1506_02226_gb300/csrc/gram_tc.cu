@@ -908,25 +908,33 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
 // ---------------- preparation kernels ----------------
 
 // Grid check and centred integer rows: v16[i][k] = u - 512 (pads 0), |v|^2.
+// A warp per row (lane k reads coordinate k, then k + 32), so the input rows
+// are read coalesced.
 __global__ void tc_prep_kernel(const float *__restrict__ x, int n, int d, int K, int16_t *__restrict__ v16,
                                int *__restrict__ nrm, unsigned *status) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int s = 0;
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
     bool ok = true;
-    for (int k = 0; k < K; ++k) {
-        int v = 0;
-        if (k < d) {
-            int u;
-            ok &= db::on_grid(x[(size_t)i * d + k], u);
-            v = u - 512;
+    for (int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); i < n; i += nwarps) {
+        int s = 0;
+        for (int k = lane; k < K; k += 32) {
+            int v = 0;
+            if (k < d) {
+                int u;
+                ok &= db::on_grid(x[(size_t)i * d + k], u);
+                v = u - 512;
+            }
+            v16[(size_t)i * K + k] = (int16_t)v;
+            s += v * v;
         }
-        v16[(size_t)i * K + k] = (int16_t)v;
-        s += v * v;
+        s = __reduce_add_sync(0xffffffffu, s);
+        if (lane == 0) nrm[i] = s;
     }
-    nrm[i] = s;
-    if (!ok) atomicOr(status, DB_EBIT_NOT_QUANTISED);
+    if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicOr(status, DB_EBIT_NOT_QUANTISED);
 }
+
+// Blocks of 256 threads for tc_prep_kernel: a warp per row, at most 16 blocks per SM.
+int tc_prep_blocks(int n) { return (int)std::min<int64_t>(((int64_t)n + 7) / 8, 152 * 16); }
 
 __device__ __forceinline__ uint16_t fp16_bits(int v) {
     __half h = __int2half_rn(v);
@@ -1055,7 +1063,7 @@ cudaError_t launch_allpairs_tc(const DbWork &w, const float *x, int64_t n64, int
     const int nb = (n + 255) / 256;
     int *lens = w.tc_lens;  // [0] all, [1] core, [2] non-core
     set_len_kernel<<<1, 1, 0, st>>>(lens + 2, n);
-    tc_prep_kernel<<<nb, 256, 0, st>>>(x, n, d, K, w.v16, w.inorm, w.status);
+    tc_prep_kernel<<<tc_prep_blocks(n), 256, 0, st>>>(x, n, d, K, w.v16, w.inorm, w.status);
     w.marks->kernel("tc_prep", st);
     const int pack_blocks = (int)std::min<int64_t>(((int64_t)n_pad * (K / 8) + 255) / 256, 152 * 32);
     tc_pack_kernel<<<pack_blocks, 256, 0, st>>>(nullptr, lens + 2, n_pad, K, bf16, w.v16, w.inorm, w.opAll,
@@ -1142,7 +1150,7 @@ cudaError_t launch_tc_verify(const DbWork &w, const float *x, int64_t n64, int32
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int *lens = w.tc_lens;
     set_len_kernel<<<1, 1, 0, st>>>(lens + 2, n);
-    tc_prep_kernel<<<(n + 255) / 256, 256, 0, st>>>(x, n, d, K, w.v16, w.inorm, w.status);
+    tc_prep_kernel<<<tc_prep_blocks(n), 256, 0, st>>>(x, n, d, K, w.v16, w.inorm, w.status);
     const int pack_blocks = (int)std::min<int64_t>(((int64_t)n_pad * (K / 8) + 255) / 256, 152 * 32);
     tc_pack_kernel<<<pack_blocks, 256, 0, st>>>(nullptr, lens + 2, n_pad, K, bf16, w.v16, w.inorm, w.opAll,
                                                 reinterpret_cast<MetaBlock *>(w.metaAll));
