@@ -343,13 +343,13 @@ __device__ __noinline__ int exact_sqdist(const int16_t *__restrict__ v16, int K,
 // again once its MMAs have completed; the epilogue holds only the tile's
 // metadata, in a ring of its own, so the operand ring runs up to NS tiles
 // ahead of the MMAs whatever the epilogue's pace.
-template <int KC, int NS, int NM>
+template <int KC, int NS, int NM, int RTN>
 struct __align__(16) SmemT {
     static constexpr int NSTAGE = NS;
     static constexpr int NMETA = NM;
-    uint16_t A[2][TM * KC];          // 2 x 16 KB (FP16) or 2 x 32 KB (BF16)
+    uint16_t A[2 * RTN][TM * KC];    // two buffers of RTN row tiles (16 KB each for FP16, 32 KB for BF16)
     uint16_t B[NS][TN * KC];
-    MetaBlock metaA[2];              // 2 x 2 KB
+    MetaBlock metaA[2 * RTN];        // 2 KB per row tile
     MetaBlock metaB[NM][2];          // NM x 4 KB
     uint64_t a_full[2], a_empty[2];
     uint64_t b_full[NS], b_empty[NS];
@@ -365,15 +365,25 @@ struct __align__(16) SmemT {
     int colroot[2][2][128];
 };
 
-// Work item w covers row tile rt and column tiles [c0, c1) of one column chunk.
+// Shared memory of each pass: FP16 count (two row tiles per item) 4 B stages
+// and 5 metadata stages; other FP16 passes 5 and 6; BF16 2 and 6.
+template <int PASS, bool BF16>
+struct TcSmem {
+    static constexpr bool RT2 = PASS == TC_COUNT && !BF16;
+    using type = SmemT<BF16 ? 128 : 64, BF16 ? 2 : (RT2 ? 4 : 5), RT2 ? 5 : 6, RT2 ? 2 : 1>;
+};
+
+// Work item w covers row unit rt (TMU rows: one 128-row tile, or two for the
+// FP16 count) and column tiles [c0, c1) of one column chunk.
 // Count and border passes: ch = w / nrt, rt = w % nrt, so the CTAs running at
 // one time share their column chunk and its B tiles come from L2.  Merge pass
 // (a.upper): rt = w / nchunk and the chunk rotates with the row tile, so the
 // CTAs running at one time work on different column chunks: the first visit to
 // a chunk's points unites and flattens them, and later visits find them in
 // their cluster's set (the core operand, at most n x 128 bytes, stays in L2).
+template <int TMU>
 __device__ __forceinline__ bool item_range(const TcArgs &a, int w, int nR, int nC, int &rt, int &c0, int &c1) {
-    const int nrt = (nR + TM - 1) / TM, nct = (nC + TN - 1) / TN;
+    const int nrt = (nR + TMU - 1) / TMU, nct = (nC + TN - 1) / TN;
     const int nchunk = (nct + a.col_chunk - 1) / a.col_chunk;
     if (w >= nrt * nchunk) return false;
     int ch;
@@ -386,7 +396,7 @@ __device__ __forceinline__ bool item_range(const TcArgs &a, int w, int nR, int n
     }
     c0 = ch * a.col_chunk;
     c1 = min(nct, c0 + a.col_chunk);
-    if (a.upper) c0 = max(c0, (rt * TM) / TN);  // pairs i < j only: skip tiles left of the diagonal
+    if (a.upper) c0 = max(c0, (rt * TMU) / TN);  // pairs i < j only: skip tiles left of the diagonal
     return true;
 }
 
@@ -410,7 +420,11 @@ __device__ __noinline__ int unite_root(int *parent, int p, int q, unsigned *stat
 template <int PASS, bool BF16>
 __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(TcArgs a) {
     constexpr int EPI_WARPS = epi_warps<PASS, BF16>();
-    // FP16 count: two groups of four warps take alternate tiles (a group per accumulator buffer)
+    // FP16 count: each work item holds two row tiles, so every B tile feeds two
+    // MMA tiles, one per accumulator buffer, and two groups of four warps
+    // drain them, a group per buffer (and row tile).
+    constexpr int RTN = (PASS == TC_COUNT && !BF16) ? 2 : 1;
+    constexpr int TMU = TM * RTN;
     constexpr int EPI_GROUPS = (PASS == TC_COUNT && !BF16) ? 2 : 1;
     constexpr int TILE_WARPS = EPI_WARPS / EPI_GROUPS;  // epilogue warps that read one tile
     constexpr int GW = group_cols<PASS, BF16>();    // columns per group
@@ -419,12 +433,12 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
     // Align by pointer arithmetic on the shared array (not through an integer),
     // so the compiler keeps shared-space loads, stores and atomics.
     const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
-    using Smem = SmemT<BF16 ? 128 : 64, BF16 ? 2 : 5, 6>;
+    using Smem = typename TcSmem<PASS, BF16>::type;
     constexpr int NSTAGE = Smem::NSTAGE, NMETA = Smem::NMETA;
     Smem &S = *reinterpret_cast<Smem *>(smem_raw + pad);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nR = *a.nR_ptr, nC = *a.nC_ptr;
-    const int nrt = (nR + TM - 1) / TM, nct = (nC + TN - 1) / TN;
+    const int nrt = (nR + TMU - 1) / TMU, nct = (nC + TN - 1) / TN;
     const int nchunk = (nct + a.col_chunk - 1) / a.col_chunk;
     const int nitems = nrt * nchunk;
     if ((int)blockIdx.x >= nitems) return;  // nothing for this CTA (before any TMEM use)
@@ -441,7 +455,7 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
             mbar_init(&S.b_full[i], 1);
             mbar_init(&S.b_empty[i], 1);  // the MMA commit of the tile
         }
-        for (int i = 0; i < NMETA; ++i) mbar_init(&S.m_empty[i], TILE_WARPS);
+        for (int i = 0; i < NMETA; ++i) mbar_init(&S.m_empty[i], RTN == 2 ? EPI_WARPS : TILE_WARPS);
         mbar_init(&S.drain, 1);
         S.abort_flag = 0;
         S.drain_failed = 0;
@@ -470,12 +484,13 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
             for (int s = 0; s < NSTAGE; ++s) last_b[s] = -1;
             for (int w = blockIdx.x; w < nitems && !*abort_flag; w += gridDim.x, ++ia) {
                 int rt, c0, c1;
-                item_range(a, w, nR, nC, rt, c0, c1);
+                item_range<TMU>(a, w, nR, nC, rt, c0, c1);
                 const int ab = ia & 1;
                 if (!mbar_wait(&S.a_empty[ab], ((ia >> 1) & 1) ^ 1, abort_flag, a.wait_ns)) break;
-                mbar_arrive_expect_tx(&S.a_full[ab], a_bytes + sizeof(MetaBlock));
-                bulk_g2s(S.A[ab], a.opR + (size_t)rt * TM * KS, a_bytes, &S.a_full[ab]);
-                bulk_g2s(&S.metaA[ab], a.metaR + rt, sizeof(MetaBlock), &S.a_full[ab]);
+                // RTN consecutive row tiles (the packed list holds whole 256-row tiles)
+                mbar_arrive_expect_tx(&S.a_full[ab], RTN * (a_bytes + (uint32_t)sizeof(MetaBlock)));
+                bulk_g2s(S.A[ab * RTN], a.opR + (size_t)rt * RTN * TM * KS, RTN * a_bytes, &S.a_full[ab]);
+                bulk_g2s(&S.metaA[ab * RTN], a.metaR + rt * RTN, RTN * (uint32_t)sizeof(MetaBlock), &S.a_full[ab]);
                 last_a[ab] = ia >> 1;
                 for (int ct = c0; ct < c1; ++ct, ++t) {
                     const int s = t % NSTAGE, m = t % NMETA;
@@ -513,37 +528,49 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
             unsigned long long evaluated = 0;  // pairs of the tiles multiplied
             for (int w = blockIdx.x; w < nitems && !*abort_flag; w += gridDim.x, ++ia) {
                 int rt, c0, c1;
-                item_range(a, w, nR, nC, rt, c0, c1);
+                item_range<TMU>(a, w, nR, nC, rt, c0, c1);
                 const int ab = ia & 1;
                 if (!mbar_wait(&S.a_full[ab], (ia >> 1) & 1, abort_flag, a.wait_ns)) break;
-                const uint32_t a_addr = smem_u32(S.A[ab]);
                 bool ok = true;
-                for (int ct = c0; ct < c1; ++ct, ++t) {
-                    const int s = t % NSTAGE, b = t & 1;
-                    if (!TC_WAIT(w_mma_b, mbar_wait(&S.b_full[s], (t / NSTAGE) & 1, abort_flag, a.wait_ns)) ||
-                        !TC_WAIT(w_mma_t, mbar_wait(&S.t_empty[b], ((t >> 1) & 1) ^ 1, abort_flag, a.wait_ns))) {
+                for (int ct = c0; ct < c1 && ok; ++ct, ++t) {
+                    const int s = t % NSTAGE;
+                    if (!TC_WAIT(w_mma_b, mbar_wait(&S.b_full[s], (t / NSTAGE) & 1, abort_flag, a.wait_ns))) {
                         ok = false;
                         break;
                     }
-                    tc_fence_after();
                     const uint32_t b_addr = smem_u32(S.B[s]);
-                    // FP16: sum over K of v_p v_q.  BF16: hi.hi + hi.lo + lo.hi, the
-                    // lo columns K/16 chunks after the hi ones (256 B per chunk).
-                    const int kch = K / 16;
-                    for (int kk = 0; kk < kch; ++kk) {
-                        const uint64_t ad = smem_desc(a_addr + kk * 256, KG * 128);
-                        const uint64_t bd = smem_desc(b_addr + kk * 256, KG * 128);
-                        mma_f16(tmem + (uint32_t)(b * TN), ad, bd, idesc, kk > 0 ? 1u : 0u);
-                        if (BF16) {
-                            const uint64_t bl = smem_desc(b_addr + (kch + kk) * 256, KG * 128);
-                            const uint64_t al = smem_desc(a_addr + (kch + kk) * 256, KG * 128);
-                            mma_f16(tmem + (uint32_t)(b * TN), ad, bl, idesc, 1u);
-                            mma_f16(tmem + (uint32_t)(b * TN), al, bd, idesc, 1u);
+                    for (int r = 0; r < RTN; ++r) {
+                        // accumulator buffer and its use count: with two row tiles each
+                        // buffer serves one of them on every B tile; otherwise the
+                        // buffers alternate between tiles
+                        const int b = RTN == 2 ? r : (t & 1), use = RTN == 2 ? t : (t >> 1);
+                        if (!TC_WAIT(w_mma_t, mbar_wait(&S.t_empty[b], (use & 1) ^ 1, abort_flag, a.wait_ns))) {
+                            ok = false;
+                            break;
                         }
+                        tc_fence_after();
+                        // the RTN row tiles lie back to back (a_bytes each) from the buffer's start
+                        const uint32_t a_addr = smem_u32(S.A[ab * RTN]) + (uint32_t)r * a_bytes;
+                        // FP16: sum over K of v_p v_q.  BF16: hi.hi + hi.lo + lo.hi, the
+                        // lo columns K/16 chunks after the hi ones (256 B per chunk).
+                        const int kch = K / 16;
+                        for (int kk = 0; kk < kch; ++kk) {
+                            const uint64_t ad = smem_desc(a_addr + kk * 256, KG * 128);
+                            const uint64_t bd = smem_desc(b_addr + kk * 256, KG * 128);
+                            mma_f16(tmem + (uint32_t)(b * TN), ad, bd, idesc, kk > 0 ? 1u : 0u);
+                            if (BF16) {
+                                const uint64_t bl = smem_desc(b_addr + (kch + kk) * 256, KG * 128);
+                                const uint64_t al = smem_desc(a_addr + (kch + kk) * 256, KG * 128);
+                                mma_f16(tmem + (uint32_t)(b * TN), ad, bl, idesc, 1u);
+                                mma_f16(tmem + (uint32_t)(b * TN), al, bd, idesc, 1u);
+                            }
+                        }
+                        mma_commit(&S.t_full[b]);  // accumulator ready for the epilogue
+                        evaluated += (unsigned long long)max(0, min(TM, nR - (rt * RTN + r) * TM)) *
+                                     min(TN, nC - ct * TN);
                     }
-                    mma_commit(&S.t_full[b]);   // accumulator ready for the epilogue
+                    if (!ok) break;
                     mma_commit(&S.b_empty[s]);  // operands of this stage consumed
-                    evaluated += (unsigned long long)min(TM, nR - rt * TM) * min(TN, nC - ct * TN);
                 }
                 mma_commit(&S.a_empty[ab]);
                 if (!ok) {
@@ -586,14 +613,17 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
         unsigned maxerr = 0;
         for (int w = blockIdx.x; w < nitems; w += gridDim.x, ++ia) {
             int rt, c0, c1;
-            item_range(a, w, nR, nC, rt, c0, c1);
+            item_range<TMU>(a, w, nR, nC, rt, c0, c1);
             const int ab = ia & 1;
+            // the row tile of the item this warp serves (its group's, with two)
+            const int rsel = RTN == 2 ? ew / TILE_WARPS : 0;
             if (!__all_sync(0xffffffffu, mbar_wait(&S.a_full[ab], (ia >> 1) & 1, abort_flag, a.wait_ns))) break;
-            const float beta_p = S.metaA[ab].beta[r], rho_p = S.metaA[ab].rho[r];
-            const int p = S.metaA[ab].idx[r];
+            const MetaBlock &ma = S.metaA[ab * RTN + rsel];
+            const float beta_p = ma.beta[r], rho_p = ma.rho[r];
+            const int p = ma.idx[r];
             __syncwarp();
             if (lane == 0) mbar_arrive(&S.a_empty[ab]);
-            const int i_row = rt * TM + r;  // list index of this row
+            const int i_row = (rt * RTN + rsel) * TM + r;  // list index of this row
             const bool row_ok = i_row < nR && p >= 0;
             const float alpha = beta_p - (float)a.T;  // |v_p|^2 - T, exact
             int cnt = 0, bmin = INT_MAX;
@@ -601,13 +631,14 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
             int rootp = (PASS == TC_UNION && row_ok) ? db::ld_relaxed(a.parent + p) : -2;
             bool ok = true;
             for (int ct = c0; ct < c1; ++ct, ++t) {
-                const int m = t % NMETA, b = t & 1;
-                if (EPI_GROUPS == 2 && b != (ew >> 2)) continue;  // the other group's tile
+                // accumulator buffer of this warp's tile and its use count (see the MMA issuer)
+                const int m = t % NMETA, b = RTN == 2 ? rsel : (t & 1), use = RTN == 2 ? t : (t >> 1);
+                if (RTN == 1 && EPI_GROUPS == 2 && b != ew / TILE_WARPS) continue;  // the other group's tile
                 // warp-uniform outcome: the accumulator loads below are warp-collective
                 // the accumulator is usually ready: test once inline before the bounded wait
                 if (!__all_sync(0xffffffffu,
-                                mbar_try_wait(&S.t_full[b], (t >> 1) & 1) ||
-                                    TC_WAIT(w_epi, mbar_wait(&S.t_full[b], (t >> 1) & 1, abort_flag, a.wait_ns)))) {
+                                mbar_try_wait(&S.t_full[b], use & 1) ||
+                                    TC_WAIT(w_epi, mbar_wait(&S.t_full[b], use & 1, abort_flag, a.wait_ns)))) {
                     ok = false;
                     break;
                 }
@@ -1026,9 +1057,9 @@ __global__ void core_flags_kernel(int n, const uint8_t *__restrict__ core, int *
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) flags[i] = core[i];
 }
 
-template <bool BF16>
+template <int PASS, bool BF16>
 size_t tc_smem_bytes() {
-    return sizeof(SmemT<BF16 ? 128 : 64, BF16 ? 2 : 5, 6>) + 1024;
+    return sizeof(typename TcSmem<PASS, BF16>::type) + 1024;
 }
 
 template <int PASS, bool BF16>
@@ -1036,11 +1067,11 @@ cudaError_t launch_pass_t(const TcArgs &a, int sms, cudaStream_t st) {
     static bool attr = false;  // one process-wide attribute per instantiation
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(tc_pass_kernel<PASS, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)tc_smem_bytes<BF16>());
+                                             (int)tc_smem_bytes<PASS, BF16>());
         if (e) return e;
         attr = true;
     }
-    tc_pass_kernel<PASS, BF16><<<sms, tc_threads<PASS, BF16>(), tc_smem_bytes<BF16>(), st>>>(a);
+    tc_pass_kernel<PASS, BF16><<<sms, tc_threads<PASS, BF16>(), tc_smem_bytes<PASS, BF16>(), st>>>(a);
     return cudaGetLastError();
 }
 
