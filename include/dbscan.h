@@ -216,7 +216,8 @@ int dbscan_tc_verify(dbscan_plan *plan, const float *points, int64_t n, int32_t 
  * rechecked exactly; slots 16..19 count the pair predicates evaluated by the
  * count, merge, border and (eps-grid path) outer-ring merge passes (their sum
  * is dbscan_stats.pair_tests);
- * builds made for pipeline diagnostics fill slots 9..13 with cycles spent
+ * builds made for pipeline diagnostics fill slots 9..13, 20..24 and 25..29
+ * (tensor-core count, merge and border passes) with cycles spent
  * blocked per pipeline role.  Waits for the plan's stream. */
 int dbscan_plan_counters(dbscan_plan *plan, uint64_t *out, int32_t n);
 

@@ -231,7 +231,8 @@ __device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsig
 }
 
 // Optional pipeline diagnostics (compile with -DDB_TC_WAIT_STATS): cycles each
-// role spends blocked on each barrier, summed into ctr[9..14].
+// role spends blocked on each barrier, summed per pass into the counters
+// listed at the end of the kernel.
 #ifdef DB_TC_WAIT_STATS
 #define TC_WAIT(acc, expr) ({ long long _t0 = clock64(); bool _r = (expr); acc += clock64() - _t0; _r; })
 #else
@@ -907,13 +908,18 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
     }
 
 #ifdef DB_TC_WAIT_STATS
-    if (threadIdx.x == 0) atomicAdd(a.ctr + 9, (unsigned long long)w_prod);
-    if (threadIdx.x == 32) {
-        atomicAdd(a.ctr + 10, (unsigned long long)w_mma_b);
-        atomicAdd(a.ctr + 11, (unsigned long long)w_mma_t);
-        atomicAdd(a.ctr + 13, (unsigned long long)(clock64() - t_start));
+    // slots 9..13 (count), 20..24 (merge), 25..29 (border): producer, MMA issuer
+    // on B tiles, MMA issuer on accumulators, one epilogue warp, issuer total
+    {
+        unsigned long long *ws = a.ctr + (PASS == TC_COUNT ? 9 : (PASS == TC_UNION ? 20 : 25));
+        if (PASS != TC_VERIFY && threadIdx.x == 0) atomicAdd(ws, (unsigned long long)w_prod);
+        if (PASS != TC_VERIFY && threadIdx.x == 32) {
+            atomicAdd(ws + 1, (unsigned long long)w_mma_b);
+            atomicAdd(ws + 2, (unsigned long long)w_mma_t);
+            atomicAdd(ws + 4, (unsigned long long)(clock64() - t_start));
+        }
+        if (PASS != TC_VERIFY && threadIdx.x == 64) atomicAdd(ws + 3, (unsigned long long)w_epi);
     }
-    if (threadIdx.x == 64) atomicAdd(a.ctr + 12, (unsigned long long)w_epi);
 #endif
     // ---------------- teardown ----------------
     tc_fence_before();

@@ -21,7 +21,8 @@
 
 // Device counters of a run (DbWork::ctr, DB_NCTR 64-bit slots):
 //   0 grid cells|points, 1 grid candidate pairs, 2..5 core/border/noise/clusters,
-//   6 band pairs rechecked, 7..8 band verification, 9..13 pipeline diagnostics,
+//   6 band pairs rechecked, 7..8 band verification, 9..13 and 20..29 pipeline
+//   diagnostics of the tensor-core count, merge and border passes,
 //   16..19 pair tests evaluated by the count, merge, border and (grid path)
 //   outer-ring merge passes, 31 work items of the projected grid (int).
 #define DB_NCTR 32
