@@ -76,15 +76,15 @@ __host__ __device__ constexpr int bf16_band(int K) { return 16 * K; }
 enum { TC_COUNT = 0, TC_UNION = 1, TC_BORDER = 2, TC_VERIFY = 3 };
 
 // Epilogue warps per CTA.  The FP16 count: two groups of four warps (one per
-// TMEM lane quadrant) take alternate tiles, one group per accumulator buffer,
-// and each warp decides all 256 columns of its rows, loading 32 columns ahead
-// of the ones it decides; the two groups' phases drift apart, so one group's
-// loads overlap the other's arithmetic (measured against the alternatives: four
-// warps of 64 columns per quadrant 6.75 ms, two of 128 on every tile 6.27,
-// this 6.14, sixteen warps in two groups 6.30).  Merge, border and BF16: four
-// per quadrant (64 columns each, in groups of 32: the candidate scores and the
-// accumulator copy fit the 16-warp register budget).  Verification: two per
-// quadrant, groups of 64.
+// TMEM lane quadrant), one group per row tile of the item and accumulator
+// buffer, and each warp decides all 256 columns of its rows, loading 32
+// columns ahead of the ones it decides (measured against the alternatives,
+// with one row tile per item: four warps of 64 columns per quadrant 6.75 ms,
+// two of 128 on every tile 6.27, this 6.14, sixteen warps in two groups 6.30).
+// FP16 border: two groups of eight, two warps per quadrant of 128 columns
+// each.  Merge and BF16: four per quadrant (64 columns each).  Groups of 32
+// columns in both (the candidate scores and the accumulator copy fit the
+// 16-warp register budget).  Verification: two per quadrant, groups of 64.
 template <int PASS, bool BF16>
 constexpr int epi_warps() {
     return (PASS == TC_COUNT && !BF16) ? 8 : (PASS != TC_VERIFY ? 16 : 8);
@@ -366,11 +366,12 @@ struct __align__(16) SmemT {
     int colroot[2][2][128];
 };
 
-// Shared memory of each pass: FP16 count (two row tiles per item) 4 B stages
-// and 5 metadata stages; other FP16 passes 5 and 6; BF16 2 and 6.
+// Shared memory of each pass: FP16 count and border (two row tiles per item)
+// 4 B stages and 5 metadata stages; FP16 merge and verification 5 and 6; BF16
+// 2 and 6.
 template <int PASS, bool BF16>
 struct TcSmem {
-    static constexpr bool RT2 = PASS == TC_COUNT && !BF16;
+    static constexpr bool RT2 = !BF16 && (PASS == TC_COUNT || PASS == TC_BORDER);
     using type = SmemT<BF16 ? 128 : 64, BF16 ? 2 : (RT2 ? 4 : 5), RT2 ? 5 : 6, RT2 ? 2 : 1>;
 };
 
@@ -421,15 +422,16 @@ __device__ __noinline__ int unite_root(int *parent, int p, int q, unsigned *stat
 template <int PASS, bool BF16>
 __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(TcArgs a) {
     constexpr int EPI_WARPS = epi_warps<PASS, BF16>();
-    // FP16 count: each work item holds two row tiles, so every B tile feeds two
-    // MMA tiles, one per accumulator buffer, and two groups of four warps
-    // drain them, a group per buffer (and row tile).
-    constexpr int RTN = (PASS == TC_COUNT && !BF16) ? 2 : 1;
+    // FP16 count and border: each work item holds two row tiles, so every B
+    // tile feeds two MMA tiles, one per accumulator buffer, and two groups of
+    // epilogue warps drain them, a group per buffer (and row tile).
+    constexpr int RTN = (!BF16 && (PASS == TC_COUNT || PASS == TC_BORDER)) ? 2 : 1;
     constexpr int TMU = TM * RTN;
-    constexpr int EPI_GROUPS = (PASS == TC_COUNT && !BF16) ? 2 : 1;
+    constexpr int EPI_GROUPS = (PASS == TC_COUNT && !BF16) || RTN == 2 ? 2 : 1;
     constexpr int TILE_WARPS = EPI_WARPS / EPI_GROUPS;  // epilogue warps that read one tile
     constexpr int GW = group_cols<PASS, BF16>();    // columns per group
-    constexpr int NG = (1024 / EPI_WARPS) / GW;     // groups per epilogue warp and tile
+    constexpr int WPQ = TILE_WARPS / 4;             // warps per lane quadrant on one tile
+    constexpr int NG = (TN / WPQ) / GW;             // groups per epilogue warp and tile
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // Align by pointer arithmetic on the shared array (not through an integer),
     // so the compiler keeps shared-space loads, stores and atomics.
@@ -604,7 +606,7 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
         // ---------------- epilogue ----------------
         const int ew = warp - 2;                  // 0..EPI_WARPS-1
         const int quad = warp & 3;                // TMEM lane quadrant this warp may access
-        const int colbase = (ew >> 2) * (1024 / EPI_WARPS);  // first column of this warp in the tile
+        const int colbase = ((ew >> 2) % WPQ) * (TN / WPQ);  // first column of this warp in the tile
         const int half = colbase >> 7;            // 128-column metadata block holding it
         const int moff = colbase & 127;           // its offset in that block
         const int r = quad * 32 + lane;           // row within the tile
