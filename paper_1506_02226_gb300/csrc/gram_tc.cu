@@ -794,8 +794,8 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
                     // by kBf16FilterSlack to cover them, and the rare path decides.
                     const float thr = BF16 ? alpha - kBf16FilterSlack : alpha - (float)FP16_BAND;
                     float mx;
+                    float nv[GW];  // after the tree, nv[i] = minimum over the columns j = i (mod 8)
                     {
-                        float nv[GW];
                         const unsigned long long m2 = f2_pack(-2.f, -2.f);
 #pragma unroll
                         for (int j4 = 0; j4 < GW / 4; ++j4) {
@@ -835,15 +835,29 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
                     // columns never pass, their beta is 1e30).  The merge pass also
                     // drops the columns whose set hint equals the row's: those pairs
                     // need no union.
+                    // Only the residues j mod 8 whose minimum passes the filter in
+                    // some lane of the warp are scanned (warp-uniform branches, so the
+                    // column indices stay compile-time constants).
                     uint64_t mask = 0;
-                    if (need) {
+                    {
+                        unsigned rm = 0;
+                        if (need) {
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) rm |= (unsigned)(-nv[i] >= thr) << i;
+                        }
+                        const unsigned um = __reduce_or_sync(0xffffffffu, rm);
                         const int col_lim = a.upper ? (i_row - (ct * TN + half * 128)) : -1;  // cols <= this: j <= i
 #pragma unroll
-                        for (int j = 0; j < GW; ++j) {
-                            const float w1 = fmaf(2.f, __uint_as_float(g[j]), -mc.beta[cb + j]);
-                            bool c = BF16 ? (fmaf(rho_p, mc.rho[cb + j], w1) >= alpha) : (w1 >= alpha);
-                            if (PASS == TC_UNION) c = c && colroot[cb + j] != rootp;
-                            mask |= (uint64_t)(c && (cb + j) > col_lim) << j;
+                        for (int i = 0; i < 8; ++i) {
+                            if (!((um >> i) & 1u)) continue;
+#pragma unroll
+                            for (int u = 0; u < GW / 8; ++u) {
+                                const int j = i + 8 * u;
+                                const float w1 = fmaf(2.f, __uint_as_float(g[j]), -mc.beta[cb + j]);
+                                bool c = need && (BF16 ? (fmaf(rho_p, mc.rho[cb + j], w1) >= alpha) : (w1 >= alpha));
+                                if (PASS == TC_UNION) c = c && colroot[cb + j] != rootp;
+                                mask |= (uint64_t)(c && (cb + j) > col_lim) << j;
+                            }
                         }
                     }
                     uint64_t nbm = mask;  // confirmed neighbours among the mask
