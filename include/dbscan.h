@@ -213,7 +213,10 @@ int dbscan_tc_verify(dbscan_plan *plan, const float *points, int64_t n, int32_t 
 
 /* Raw device counters of the plan's last run (diagnostics): copies up to n of
  * the plan's 32 64-bit counters to out (host).  Slot 6 counts band pairs
- * rechecked exactly; slots 16..19 count the pair predicates evaluated by the
+ * rechecked exactly; slot 15 is 1 when the FP16 tensor-core count pass ran
+ * its folded form (the column norm subtracted inside the MMA, used when
+ * 3 max|v|^2 + 1 <= 2^25 for the centred units v = u - 512, which keeps it
+ * exact); slots 16..19 count the pair predicates evaluated by the
  * count, merge, border and (eps-grid path) outer-ring merge passes (their sum
  * is dbscan_stats.pair_tests);
  * builds made for pipeline diagnostics fill slots 9..13, 20..24 and 25..29

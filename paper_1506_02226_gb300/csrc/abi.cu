@@ -85,7 +85,9 @@ size_t layout(DbWork &w, const dbscan_opts &o, char *base) {
         w.occ_cap = 0;
     }
     if (o.max_d >= 16) {
-        const int64_t np = (n + 255) / 256 * 256;
+        // one more 256-row tile than n needs: the FP16 count's column list leaves
+        // a gap of up to 255 rows between its even-norm and odd-norm points
+        const int64_t np = (n + 255) / 256 * 256 + 256;
         w.tc_cap_pad = np;
         w.v16 = c.take<int16_t>((size_t)n * 64);
         w.inorm = c.take<int32_t>(n);
@@ -95,9 +97,9 @@ size_t layout(DbWork &w, const dbscan_opts &o, char *base) {
         w.metaAll = c.take<char>((size_t)np * 16);
         w.metaCore = c.take<char>((size_t)np * 16);
         w.metaNon = c.take<char>((size_t)np * 16);
-        w.list_a = c.take<int32_t>(n);
+        w.list_a = c.take<int32_t>(np);
         w.list_b = c.take<int32_t>(n);
-        w.tc_lens = c.take<int32_t>(4);
+        w.tc_lens = c.take<int32_t>(8);
     } else {
         w.tc_cap_pad = 0;
     }

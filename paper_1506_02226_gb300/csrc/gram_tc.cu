@@ -117,11 +117,14 @@ struct TcArgs {
     const int *nR_ptr;    // device-side list lengths
     const int *nC_ptr;
     int K;                // padded dimension (multiple of 16, <= 64)
+    int ks;               // stored operand columns per row: K, 2K (BF16 terms) or K + 16 (FP16 count)
     int T;                // threshold (< 2^24)
     int bf16;
     int pass;
     int upper;                   // union: only pairs i < j of one list
     unsigned long long wait_ns;  // budget of every barrier wait
+    const int *bmax_ptr;  // FP16 count: largest |v|^2 of the input (decides the folded form)
+    const int *nE_ptr;    // FP16 count: even-norm points at the head of the column list
     int stall;                   // test hook: the MMA issuer issues nothing
     const int16_t *v16;   // centred units by point index, row stride K (exact recheck)
     int *count;
@@ -344,7 +347,7 @@ __device__ __noinline__ int exact_sqdist(const int16_t *__restrict__ v16, int K,
 // again once its MMAs have completed; the epilogue holds only the tile's
 // metadata, in a ring of its own, so the operand ring runs up to NS tiles
 // ahead of the MMAs whatever the epilogue's pace.
-template <int KC, int NS, int NM, int RTN>
+template <int KC, int NS, int NM, int RTN, int CR>
 struct __align__(16) SmemT {
     static constexpr int NSTAGE = NS;
     static constexpr int NMETA = NM;
@@ -360,19 +363,22 @@ struct __align__(16) SmemT {
     uint32_t tmem_base;
     int abort_flag;
     int drain_failed;                // a role's bounded drain wait gave up
-    // union pass: hints of the column points' sets, per accumulator buffer and
-    // column half (shared by the four warps of a half; a buffer is refilled only
-    // after all eight epilogue warps have released it)
-    int colroot[2][2][128];
+    // union pass (CR = 512): hints of the column points' sets, per accumulator
+    // buffer and column half (128 each, shared by the four warps of a half; a
+    // buffer is refilled only after all its epilogue warps have released it)
+    int colroot[CR];
 };
 
-// Shared memory of each pass: FP16 count and border (two row tiles per item)
-// 4 B stages and 5 metadata stages; FP16 merge and verification 5 and 6; BF16
-// 2 and 6.
+// Shared memory of each pass.  FP16 count: two row tiles per item of K + 16
+// stored columns (the folded chunk, below), 3 B stages of 40 KB and 4 metadata
+// stages; FP16 border: two row tiles, 4 and 5; FP16 merge and verification 5
+// and 6; BF16 2 and 6.
 template <int PASS, bool BF16>
 struct TcSmem {
     static constexpr bool RT2 = !BF16 && (PASS == TC_COUNT || PASS == TC_BORDER);
-    using type = SmemT<BF16 ? 128 : 64, BF16 ? 2 : (RT2 ? 4 : 5), RT2 ? 5 : 6, RT2 ? 2 : 1>;
+    static constexpr bool C16 = !BF16 && PASS == TC_COUNT;
+    using type = SmemT<BF16 ? 128 : (C16 ? 80 : 64), BF16 ? 2 : (C16 ? 3 : (RT2 ? 4 : 5)),
+                       C16 ? 4 : (RT2 ? 5 : 6), RT2 ? 2 : 1, PASS == TC_UNION ? 512 : 1>;
 };
 
 // Work item w covers row unit rt (TMU rows: one 128-row tile, or two for the
@@ -473,8 +479,18 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
     tc_fence_after();
     const uint32_t tmem = S.tmem_base;
     const int K = a.K;
-    const int KS = BF16 ? 2 * K : K;  // stored columns per row: [hi | lo] for BF16
+    const int KS = a.ks;  // stored columns per row: v, [hi | lo] (BF16) or [v | folded chunk] (FP16 count)
     const int KG = KS / 8;
+    // FP16 count: the column term folded into the MMA when the input's norms
+    // keep it exact (3 max|v|^2 + 1 <= 2^25, see the count epilogue), and the
+    // column tiles [0, ctE) that hold the even-norm points.
+    bool fold = false;
+    int nE = 0, ctE = 0;
+    if constexpr (PASS == TC_COUNT && !BF16) {
+        fold = 3ll * (long long)*a.bmax_ptr + 1 <= (1ll << 25);
+        nE = *a.nE_ptr;
+        ctE = (nE + TN - 1) / TN;
+    }
     long long w_prod = 0, w_mma_b = 0, w_mma_t = 0, w_epi = 0, t_start = clock64();
     (void)w_prod, (void)w_mma_b, (void)w_mma_t, (void)w_epi, (void)t_start;
     const uint32_t a_bytes = (uint32_t)(TM * KS * 2), b_bytes = (uint32_t)(TN * KS * 2);
@@ -557,7 +573,8 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
                         // FP16: sum over K of v_p v_q.  BF16: hi.hi + hi.lo + lo.hi, the
                         // lo columns K/16 chunks after the hi ones (256 B per chunk).
                         const int kch = K / 16;
-                        for (int kk = 0; kk < kch; ++kk) {
+                        const int kmma = fold ? KS / 16 : kch;  // the folded chunk follows the K columns of v
+                        for (int kk = 0; kk < kmma; ++kk) {
                             const uint64_t ad = smem_desc(a_addr + kk * 256, KG * 128);
                             const uint64_t bd = smem_desc(b_addr + kk * 256, KG * 128);
                             mma_f16(tmem + (uint32_t)(b * TN), ad, bd, idesc, kk > 0 ? 1u : 0u);
@@ -569,8 +586,10 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
                             }
                         }
                         mma_commit(&S.t_full[b]);  // accumulator ready for the epilogue
-                        evaluated += (unsigned long long)max(0, min(TM, nR - (rt * RTN + r) * TM)) *
-                                     min(TN, nC - ct * TN);
+                        // (FP16 count: the gap between the even and odd points holds no pairs)
+                        const int ncols = (PASS == TC_COUNT && !BF16 && ct < ctE) ? min(TN, nE - ct * TN)
+                                                                                 : min(TN, nC - ct * TN);
+                        evaluated += (unsigned long long)max(0, min(TM, nR - (rt * RTN + r) * TM)) * ncols;
                     }
                     if (!ok) break;
                     mma_commit(&S.b_empty[s]);  // operands of this stage consumed
@@ -595,6 +614,7 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
                 }
             }
             if (a.pass != TC_VERIFY && evaluated) atomicAdd(a.ctr + DB_CTR_EVAL + a.pass, evaluated);
+            if (PASS == TC_COUNT && !BF16 && fold && blockIdx.x == 0) a.ctr[DB_CTR_TC_FOLD] = 1ull;
             // After an abort: one more commit, which arrives once every MMA this
             // thread issued has completed, and a bounded wait for it.
             if (*abort_flag && t > 0) {
@@ -629,6 +649,11 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
             const int i_row = (rt * RTN + rsel) * TM + r;  // list index of this row
             const bool row_ok = i_row < nR && p >= 0;
             const float alpha = beta_p - (float)a.T;  // |v_p|^2 - T, exact
+            // folded FP16 count: 1 - thr_f for the even (f = 0) and odd (f = 1)
+            // column tiles, thr_f = ceil((|v_p|^2 - T - f) / 2) = (a_p - f + 1) >> 1
+            const int a_p = row_ok ? (int)beta_p - a.T : 0;
+            const float c_even = (float)(1 - ((a_p + 1) >> 1)), c_odd = (float)(1 - (a_p >> 1));
+            (void)c_even, (void)c_odd;
             int cnt = 0, bmin = INT_MAX;
             // union: a member of p's set (its parent, then the last root seen)
             int rootp = (PASS == TC_UNION && row_ok) ? db::ld_relaxed(a.parent + p) : -2;
@@ -647,7 +672,7 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
                 }
                 tc_fence_after();
                 const MetaBlock &mc = S.metaB[m][half];
-                int *colroot = S.colroot[b][half];
+                int *colroot = S.colroot + (PASS == TC_UNION ? (b * 2 + half) * 128 : 0);
                 bool hints = false;  // union: colroot filled for this tile
                 // union: the parents of this tile's 128 column points, loaded now so
                 // that their latency hides behind the accumulator loads and scores
@@ -663,52 +688,63 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
                     // all 256 columns in eight groups of 32: the next group's TMEM load
                     // is in flight while this group is decided
                     const uint32_t tb = tmem + lane_base + (uint32_t)(b * TN);
-                    const float c1 = 1.f - alpha;
-                    const unsigned long long m2 = f2_pack(-2.f, -2.f);
-                    unsigned long long acc[4] = {0ull, 0ull, 0ull, 0ull};
+                    unsigned long long acc[4] = {0ull, 0ull, 0ull, 0ull};  // +0.0f in both halves
                     uint32_t ga[32], gb[32];
-                    auto decide = [&](uint32_t (&g)[32], const float *bet) {
+                    auto all_groups = [&](auto &&decide) {
+                        tmem_ld32_nowait(tb, ga);
+                        tmem_wait_ld_dep(ga);
 #pragma unroll
-                        for (int j8 = 0; j8 < 4; ++j8) {
-                            const float4 ba = *reinterpret_cast<const float4 *>(bet + 8 * j8);
-                            const float4 bb = *reinterpret_cast<const float4 *>(bet + 8 * j8 + 4);
-                            const float bq[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
-#pragma unroll
-                            for (int h = 0; h < 4; ++h) {
-                                const unsigned long long w = f2_fma(
-                                    f2_pack(__uint_as_float(g[8 * j8 + 2 * h]), __uint_as_float(g[8 * j8 + 2 * h + 1])),
-                                    m2, f2_pack(bq[2 * h], bq[2 * h + 1]));
-                                float w0, w1;
-                                f2_unpack(w, w0, w1);
-                                acc[h] = f2_add(acc[h], f2_pack(__saturatef(c1 - w0), __saturatef(c1 - w1)));
-                            }
+                        for (int i = 0; i < 8; ++i) {
+                            uint32_t(&cur)[32] = (i & 1) ? gb : ga;
+                            uint32_t(&nxt)[32] = (i & 1) ? ga : gb;
+                            if (i + 1 < 8) tmem_ld32_nowait(tb + (uint32_t)(32 * (i + 1)), nxt);
+                            decide(cur, 32 * i);
+                            if (i + 1 < 8) tmem_wait_ld_dep(nxt);
                         }
                     };
-                    const float *b0 = S.metaB[m][0].beta, *b1 = S.metaB[m][1].beta;
-                    tmem_ld32_nowait(tb, ga);
-                    tmem_wait_ld_dep(ga);
-                    tmem_ld32_nowait(tb + 32, gb);
-                    decide(ga, b0);
-                    tmem_wait_ld_dep(gb);
-                    tmem_ld32_nowait(tb + 64, ga);
-                    decide(gb, b0 + 32);
-                    tmem_wait_ld_dep(ga);
-                    tmem_ld32_nowait(tb + 96, gb);
-                    decide(ga, b0 + 64);
-                    tmem_wait_ld_dep(gb);
-                    tmem_ld32_nowait(tb + 128, ga);
-                    decide(gb, b0 + 96);
-                    tmem_wait_ld_dep(ga);
-                    tmem_ld32_nowait(tb + 160, gb);
-                    decide(ga, b1);
-                    tmem_wait_ld_dep(gb);
-                    tmem_ld32_nowait(tb + 192, ga);
-                    decide(gb, b1 + 32);
-                    tmem_wait_ld_dep(ga);
-                    tmem_ld32_nowait(tb + 224, gb);
-                    decide(ga, b1 + 64);
-                    tmem_wait_ld_dep(gb);
-                    decide(gb, b1 + 96);
+                    if (fold) {
+                        // Folded form: the accumulator holds G - h_q exactly, with
+                        // h_q = ceil(|v_q|^2 / 2) (see the count's operands), and this
+                        // tile's columns share the parity f of |v_q|^2.  D <= T iff
+                        // G - h_q >= thr_f = ceil((|v_p|^2 - T - f) / 2), so
+                        // sat(acc + 1 - thr_f) is exactly 1 for a neighbour and 0
+                        // otherwise: one saturating add per pair, one packed add per
+                        // two pairs, no column data.
+                        const float cf = ct < ctE ? c_even : c_odd;
+                        all_groups([&](uint32_t(&g)[32], int) {
+#pragma unroll
+                            for (int h = 0; h < 16; ++h)
+                                acc[h & 3] = f2_add(acc[h & 3], f2_pack(__saturatef(__uint_as_float(g[2 * h]) + cf),
+                                                                        __saturatef(__uint_as_float(g[2 * h + 1]) + cf)));
+                        });
+                    } else {
+                        // G alone (exact), so sat(2G - |v_q|^2 + 1 - alpha) is exactly
+                        // 1 for a neighbour (T - D + 1 >= 1) and 0 otherwise.  Two
+                        // pairs per packed FFMA (w' = |v_q|^2 - 2G, the exact negation
+                        // of fma(2, G, -|v_q|^2): round-to-nearest is symmetric), one
+                        // saturating subtract per pair (c1 - w' = c1 + w, the same
+                        // rounding as before) and one packed add per two pairs.
+                        const float c1 = 1.f - alpha;
+                        const unsigned long long m2 = f2_pack(-2.f, -2.f);
+                        all_groups([&](uint32_t(&g)[32], int col) {
+                            const float *bet = S.metaB[m][col >> 7].beta + (col & 127);
+#pragma unroll
+                            for (int j8 = 0; j8 < 4; ++j8) {
+                                const float4 ba = *reinterpret_cast<const float4 *>(bet + 8 * j8);
+                                const float4 bb = *reinterpret_cast<const float4 *>(bet + 8 * j8 + 4);
+                                const float bq[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
+#pragma unroll
+                                for (int h = 0; h < 4; ++h) {
+                                    const unsigned long long w = f2_fma(
+                                        f2_pack(__uint_as_float(g[8 * j8 + 2 * h]), __uint_as_float(g[8 * j8 + 2 * h + 1])),
+                                        m2, f2_pack(bq[2 * h], bq[2 * h + 1]));
+                                    float w0, w1;
+                                    f2_unpack(w, w0, w1);
+                                    acc[h] = f2_add(acc[h], f2_pack(__saturatef(c1 - w0), __saturatef(c1 - w1)));
+                                }
+                            }
+                        });
+                    }
                     float sm[8];
 #pragma unroll
                     for (int h = 0; h < 4; ++h) f2_unpack(acc[h], sm[2 * h], sm[2 * h + 1]);
@@ -746,38 +782,6 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
                             if (!in_band && ((wv >= alpha) != nb_exact)) ++bad_cnt;
                             cnt += nb_exact;
                         }
-                        continue;
-                    }
-                    if (PASS == TC_COUNT && !BF16) {
-                        // FP16 count: G is exact, so sat(2G - |v_q|^2 + 1 - alpha) is
-                        // exactly 1 for a neighbour (T - D + 1 >= 1) and 0 otherwise.
-                        // Two pairs per packed FFMA (w' = |v_q|^2 - 2G, the exact
-                        // negation of fma(2, G, -|v_q|^2): round-to-nearest is
-                        // symmetric), one saturating subtract per pair (c1 - w' =
-                        // c1 + w, the same rounding as before) and one packed add per
-                        // two pairs: two FP32-pipe instructions per pair.
-                        const float c1 = 1.f - alpha;
-                        const unsigned long long m2 = f2_pack(-2.f, -2.f);
-                        unsigned long long acc[4] = {0ull, 0ull, 0ull, 0ull};  // +0.0f in both halves
-#pragma unroll
-                        for (int j8 = 0; j8 < GW / 8; ++j8) {
-                            const float4 ba = *reinterpret_cast<const float4 *>(&mc.beta[cb + 8 * j8]);
-                            const float4 bb = *reinterpret_cast<const float4 *>(&mc.beta[cb + 8 * j8 + 4]);
-                            const float bq[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
-#pragma unroll
-                            for (int h = 0; h < 4; ++h) {
-                                const unsigned long long w = f2_fma(
-                                    f2_pack(__uint_as_float(g[8 * j8 + 2 * h]), __uint_as_float(g[8 * j8 + 2 * h + 1])),
-                                    m2, f2_pack(bq[2 * h], bq[2 * h + 1]));
-                                float w0, w1;
-                                f2_unpack(w, w0, w1);
-                                acc[h] = f2_add(acc[h], f2_pack(__saturatef(c1 - w0), __saturatef(c1 - w1)));
-                            }
-                        }
-                        float s[8];
-#pragma unroll
-                        for (int h = 0; h < 4; ++h) f2_unpack(acc[h], s[2 * h], s[2 * h + 1]);
-                        if (row_ok) cnt += (int)(((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7])));
                         continue;
                     }
                     // Union / border / BF16: one FFMA per pair; the maxima of the
@@ -960,13 +964,14 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
 
 // ---------------- preparation kernels ----------------
 
-// Grid check and centred integer rows: v16[i][k] = u - 512 (pads 0), |v|^2.
-// A warp per row (lane k reads coordinate k, then k + 32), so the input rows
-// are read coalesced.
+// Grid check and centred integer rows: v16[i][k] = u - 512 (pads 0), |v|^2,
+// and the largest |v|^2 into *bmax (which starts at 0).  A warp per row (lane
+// k reads coordinate k, then k + 32), so the input rows are read coalesced.
 __global__ void tc_prep_kernel(const float *__restrict__ x, int n, int d, int K, int16_t *__restrict__ v16,
-                               int *__restrict__ nrm, unsigned *status) {
+                               int *__restrict__ nrm, unsigned *status, int *bmax) {
     const int lane = threadIdx.x & 31;
     const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    int wmax = 0;
     bool ok = true;
     for (int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); i < n; i += nwarps) {
         int s = 0;
@@ -982,8 +987,10 @@ __global__ void tc_prep_kernel(const float *__restrict__ x, int n, int d, int K,
         }
         s = __reduce_add_sync(0xffffffffu, s);
         if (lane == 0) nrm[i] = s;
+        wmax = max(wmax, s);
     }
     if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicOr(status, DB_EBIT_NOT_QUANTISED);
+    if (lane == 0 && wmax > 0) atomicMax(bmax, wmax);
 }
 
 // Blocks of 256 threads for tc_prep_kernel: a warp per row, at most 16 blocks per SM.
@@ -1001,14 +1008,31 @@ __device__ __forceinline__ int bf16_value(uint16_t bits) {
     return (int)__uint_as_float((uint32_t)bits << 16);  // an integer for every |v| <= 512
 }
 
-// Packs list entries (list == nullptr: identity) into the tiled operand layout
-// and writes their metadata; rows past the list length up to the padded
-// length become zero rows with index -1 and beta = 1e30 (never neighbours).
+// Operand modes of tc_pack_kernel: plain v (or the BF16 terms), and the two
+// sides of the folded FP16 count, which append one 16-column chunk to v.
+enum { PACK_PLAIN = 0, PACK_FOLD_ROWS = 1, PACK_FOLD_COLS = 2 };
+
+// The folded chunk.  Row side: 1, 2^11, 2^15 (then zeros).  Column side: the
+// digits of h_q = ceil(|v_q|^2 / 2) = q0 + 2^11 q1 + 2^22 q2 (q0, q1 < 2^11),
+// negated, as -q0, -q1, -2^7 q2 (then zeros); a padding column takes
+// h = 2^24.  Every entry is an integer FP16 holds exactly, and the chunk's
+// products sum to -h_q, so the MMA accumulates G - h_q.
+__device__ __forceinline__ int fold_entry(int mode, int kk, bool valid, int nrm_q) {
+    if (mode == PACK_FOLD_ROWS) return kk == 0 ? 1 : (kk == 1 ? 2048 : (kk == 2 ? 32768 : 0));
+    const int h = valid ? (nrm_q + 1) >> 1 : (1 << 24);
+    return kk == 0 ? -(h & 2047) : (kk == 1 ? -((h >> 11) & 2047) : (kk == 2 ? -((h >> 22) << 7) : 0));
+}
+
+// Packs list entries (list == nullptr: identity; an entry of -1 is padding)
+// into the tiled operand layout and writes their metadata; padding rows and
+// rows past the list length up to the padded length become zero rows with
+// index -1 and beta = 1e30 (never neighbours).
 __global__ void tc_pack_kernel(const int *__restrict__ list, const int *__restrict__ len_ptr, int n_pad, int K,
-                               int bf16, const int16_t *__restrict__ v16, const int *__restrict__ nrm,
+                               int bf16, int mode, const int16_t *__restrict__ v16, const int *__restrict__ nrm,
                                uint16_t *__restrict__ op, MetaBlock *__restrict__ meta) {
     const int len = *len_ptr;
-    const int KS = bf16 ? 2 * K : K;  // stored columns: v (FP16), or [hi | lo] (BF16)
+    // stored columns: v (FP16), [hi | lo] (BF16) or [v | folded chunk] (FP16 count)
+    const int KS = bf16 ? 2 * K : (mode != PACK_PLAIN ? K + 16 : K);
     const int KG = KS / 8, KH = K / 8;
     const float rho_c = sqrtf((float)bf16_band(K)) * (1.f + 1.f / 1024.f);
     const int64_t total = (int64_t)n_pad * KG;  // one thread per (row, 8-element group)
@@ -1017,10 +1041,15 @@ __global__ void tc_pack_kernel(const int *__restrict__ list, const int *__restri
         const int tile = i / TM, r = i - tile * TM;
         const int rg = r >> 3, ri = r & 7;
         uint16_t h[8];
-        const bool valid = i < len;
-        const int p = valid ? (list ? list[i] : i) : -1;
-        const bool lo = kg >= KH;  // BF16 only: the remainder columns
+        const int p = i < len ? (list ? list[i] : i) : -1;
+        const bool valid = p >= 0;
+        const bool lo = kg >= KH;  // BF16: the remainder columns; folded modes: the extra chunk
         const int k0 = (lo ? kg - KH : kg) * 8;
+        if (lo && mode != PACK_PLAIN) {
+            const int nq = valid ? nrm[p] : 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) h[k] = fp16_bits(fold_entry(mode, k0 + k, valid, nq));
+        } else
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             if (!valid) {
@@ -1073,7 +1102,32 @@ __global__ void tc_split_kernel(int n, const uint8_t *__restrict__ core, const i
     }
 }
 
-__global__ void set_len_kernel(int *p, int v) { *p = v; }
+// lens[2] = n (the all-points list), lens[3] = 0 (the running max of |v|^2).
+__global__ void tc_init_lens_kernel(int *lens, int n) {
+    lens[2] = n;
+    lens[3] = 0;
+}
+
+// Column list of the FP16 count: the points of even |v|^2 in index order, then,
+// from the next 256-row tile on, those of odd |v|^2; the gap holds -1.  flags
+// is the parity of each |v|^2 and scan its exclusive scan.  lens[4] = even
+// points, lens[5] = the list's length.
+__global__ void tc_parity_list_kernel(int n, const int *__restrict__ flags, const int *__restrict__ scan,
+                                      int *__restrict__ list, int *__restrict__ lens) {
+    const int n_odd = scan[n - 1] + flags[n - 1];
+    const int nE = n - n_odd, nEp = (nE + TN - 1) / TN * TN;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int i = g; i < n; i += gridDim.x * blockDim.x) list[flags[i] ? nEp + scan[i] : i - scan[i]] = i;
+    if (g < nEp - nE) list[nE + g] = -1;
+    if (g == 0) {
+        lens[4] = nE;
+        lens[5] = nEp + n_odd;
+    }
+}
+
+__global__ void tc_parity_flags_kernel(int n, const int *__restrict__ nrm, int *__restrict__ flags) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) flags[i] = nrm[i] & 1;
+}
 
 __global__ void core_flags_kernel(int n, const uint8_t *__restrict__ core, int *__restrict__ flags) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) flags[i] = core[i];
@@ -1114,19 +1168,32 @@ cudaError_t launch_allpairs_tc(const DbWork &w, const float *x, int64_t n64, int
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int nb = (n + 255) / 256;
-    int *lens = w.tc_lens;  // [0] all, [1] core, [2] non-core
-    set_len_kernel<<<1, 1, 0, st>>>(lens + 2, n);
-    tc_prep_kernel<<<tc_prep_blocks(n), 256, 0, st>>>(x, n, d, K, w.v16, w.inorm, w.status);
+    int *lens = w.tc_lens;  // [0] cores, [1] non-cores, [2] all, [3] max |v|^2, [4] even, [5] count columns
+    tc_init_lens_kernel<<<1, 1, 0, st>>>(lens, n);
+    tc_prep_kernel<<<tc_prep_blocks(n), 256, 0, st>>>(x, n, d, K, w.v16, w.inorm, w.status, lens + 3);
     w.marks->kernel("tc_prep", st);
     const int pack_blocks = (int)std::min<int64_t>(((int64_t)n_pad * (K / 8) + 255) / 256, 152 * 32);
-    tc_pack_kernel<<<pack_blocks, 256, 0, st>>>(nullptr, lens + 2, n_pad, K, bf16, w.v16, w.inorm, w.opAll,
-                                                reinterpret_cast<MetaBlock *>(w.metaAll));
+    cudaError_t e;
+    if (!bf16) {
+        // FP16 count operands: rows [v | 1, 2^11, 2^15], columns [v | -digits of
+        // ceil(|v|^2 / 2)] with the even-norm points first (see fold_entry)
+        tc_parity_flags_kernel<<<std::min(nb, 152 * 16), 256, 0, st>>>(n, w.inorm, w.list_b);
+        if ((e = launch_exclusive_scan(w.list_b, w.scan, n, w.scan_part, w.scan_part_cap, st, w.marks))) return e;
+        tc_parity_list_kernel<<<std::min(nb, 152 * 16), 256, 0, st>>>(n, w.list_b, w.scan, w.list_a, lens);
+        tc_pack_kernel<<<pack_blocks, 256, 0, st>>>(nullptr, lens + 2, n_pad, K, 0, PACK_FOLD_ROWS, w.v16, w.inorm,
+                                                    w.opAll, reinterpret_cast<MetaBlock *>(w.metaAll));
+        tc_pack_kernel<<<pack_blocks, 256, 0, st>>>(w.list_a, lens + 5, n_pad + TN, K, 0, PACK_FOLD_COLS, w.v16,
+                                                    w.inorm, w.opCore, reinterpret_cast<MetaBlock *>(w.metaCore));
+    } else {
+        tc_pack_kernel<<<pack_blocks, 256, 0, st>>>(nullptr, lens + 2, n_pad, K, 1, PACK_PLAIN, w.v16, w.inorm,
+                                                    w.opAll, reinterpret_cast<MetaBlock *>(w.metaAll));
+    }
     w.marks->kernel("tc_pack_all", st);
-    cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(int) * (size_t)n, st);
-    if (e) return e;
+    if ((e = cudaMemsetAsync(w.count, 0, sizeof(int) * (size_t)n, st))) return e;
 
     TcArgs a{};
     a.K = K;
+    a.ks = bf16 ? 2 * K : K;
     a.T = (int)Tc;
     a.bf16 = bf16 ? 1 : 0;
     a.v16 = w.v16;
@@ -1144,10 +1211,19 @@ cudaError_t launch_allpairs_tc(const DbWork &w, const float *x, int64_t n64, int
     a.opR = a.opC = w.opAll;
     a.metaR = a.metaC = reinterpret_cast<const MetaBlock *>(w.metaAll);
     a.nR_ptr = a.nC_ptr = lens + 2;
+    if (!bf16) {
+        a.ks = K + 16;
+        a.opC = w.opCore;
+        a.metaC = reinterpret_cast<const MetaBlock *>(w.metaCore);
+        a.nC_ptr = lens + 5;
+        a.nE_ptr = lens + 4;
+        a.bmax_ptr = lens + 3;
+    }
     a.pass = TC_COUNT;
     a.upper = 0;
     if ((e = launch_pass<TC_COUNT>(a, sms, st))) return e;
     w.marks->kernel("tc_count", st);
+    a.ks = bf16 ? 2 * K : K;
     a.stall = 0;
     a.wait_ns = 2000000000ull;
     // core flags, parent, border init (shared with the SIMT path)
@@ -1161,11 +1237,11 @@ cudaError_t launch_allpairs_tc(const DbWork &w, const float *x, int64_t n64, int
     }
     tc_split_kernel<<<std::min(nb, 152 * 16), 256, 0, st>>>(n, w.core, w.scan, w.list_a, w.list_b, lens);
     w.marks->kernel("tc_split", st);
-    tc_pack_kernel<<<pack_blocks, 256, 0, st>>>(w.list_a, lens + 0, n_pad, K, bf16, w.v16, w.inorm, w.opCore,
-                                                reinterpret_cast<MetaBlock *>(w.metaCore));
+    tc_pack_kernel<<<pack_blocks, 256, 0, st>>>(w.list_a, lens + 0, n_pad, K, bf16, PACK_PLAIN, w.v16, w.inorm,
+                                                w.opCore, reinterpret_cast<MetaBlock *>(w.metaCore));
     w.marks->kernel("tc_pack_core", st);
-    tc_pack_kernel<<<pack_blocks, 256, 0, st>>>(w.list_b, lens + 1, n_pad, K, bf16, w.v16, w.inorm, w.opNon,
-                                                reinterpret_cast<MetaBlock *>(w.metaNon));
+    tc_pack_kernel<<<pack_blocks, 256, 0, st>>>(w.list_b, lens + 1, n_pad, K, bf16, PACK_PLAIN, w.v16, w.inorm,
+                                                w.opNon, reinterpret_cast<MetaBlock *>(w.metaNon));
     w.marks->kernel("tc_pack_noncore", st);
     // pass 2: core x core (i < j) -> union
     a.opR = a.opC = w.opCore;
@@ -1202,14 +1278,15 @@ cudaError_t launch_tc_verify(const DbWork &w, const float *x, int64_t n64, int32
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int *lens = w.tc_lens;
-    set_len_kernel<<<1, 1, 0, st>>>(lens + 2, n);
-    tc_prep_kernel<<<tc_prep_blocks(n), 256, 0, st>>>(x, n, d, K, w.v16, w.inorm, w.status);
+    tc_init_lens_kernel<<<1, 1, 0, st>>>(lens, n);
+    tc_prep_kernel<<<tc_prep_blocks(n), 256, 0, st>>>(x, n, d, K, w.v16, w.inorm, w.status, lens + 3);
     const int pack_blocks = (int)std::min<int64_t>(((int64_t)n_pad * (K / 8) + 255) / 256, 152 * 32);
-    tc_pack_kernel<<<pack_blocks, 256, 0, st>>>(nullptr, lens + 2, n_pad, K, bf16, w.v16, w.inorm, w.opAll,
-                                                reinterpret_cast<MetaBlock *>(w.metaAll));
+    tc_pack_kernel<<<pack_blocks, 256, 0, st>>>(nullptr, lens + 2, n_pad, K, bf16, PACK_PLAIN, w.v16, w.inorm,
+                                                w.opAll, reinterpret_cast<MetaBlock *>(w.metaAll));
     if ((e = cudaMemsetAsync(w.count, 0, sizeof(int) * (size_t)n, st))) return e;
     TcArgs a{};
     a.K = K;
+    a.ks = bf16 ? 2 * K : K;
     a.T = (int)Tc;
     a.bf16 = bf16 ? 1 : 0;
     a.v16 = w.v16;

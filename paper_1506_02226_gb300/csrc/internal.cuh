@@ -23,10 +23,12 @@
 //   0 grid cells|points, 1 grid candidate pairs, 2..5 core/border/noise/clusters,
 //   6 band pairs rechecked, 7..8 band verification, 9..13 and 20..29 pipeline
 //   diagnostics of the tensor-core count, merge and border passes,
+//   15 FP16 tensor-core count ran the folded form (1),
 //   16..19 pair tests evaluated by the count, merge, border and (grid path)
 //   outer-ring merge passes, 31 work items of the projected grid (int).
 #define DB_NCTR 32
 #define DB_CTR_EVAL 16
+#define DB_CTR_TC_FOLD 15      // 1: the FP16 count ran the folded form
 #define DB_CTR_MID_ITEMS 31
 #define DB_HASH_EMPTY 0xffffffffu
 
@@ -232,13 +234,15 @@ struct DbWork {
     int32_t *cell_cand;     // points in the cells of each neighbour list [cap_n]
     int32_t noff_cap;
     // tensor-core path (max_d >= 16)
-    int64_t tc_cap_pad;     // rows of each packed operand (cap_n rounded up to 256)
+    int64_t tc_cap_pad;     // rows of each packed operand (cap_n rounded up to 256, plus 256)
     int16_t *v16;           // centred units v = u - 512 by point index, row stride 64
     int32_t *inorm;         // exact |v|^2 [cap_n]
     uint16_t *opAll, *opCore, *opNon;  // packed FP16 or two-term BF16 operand tiles [tc_cap_pad * 128]
     void *metaAll, *metaCore, *metaNon;  // per-point metadata blocks (16 B per row)
-    int32_t *list_a, *list_b;  // core / non-core index lists [cap_n]
-    int32_t *tc_lens;       // [0] cores, [1] non-cores, [2] all
+    int32_t *list_a, *list_b;  // core / non-core index lists [tc_cap_pad], [cap_n]
+    // [0] cores, [1] non-cores, [2] all, [3] largest |v|^2, [4] even-norm points,
+    // [5] length of the FP16 count's column list (even points, gap, odd points)
+    int32_t *tc_lens;
     PhaseMarks *marks;      // host-side timing marks of the owning plan
     // second stream of the grid path: independent kernels run beside each
     // other (fork/join by events); unused while per-kernel marks are taken

@@ -157,3 +157,63 @@ def test_identical_points_at_the_ends(unit):
             lab, cnt, core, st = run_plan(x, eps, 5, prec)
             assert (cnt == n).all() and core.all() and (lab == 0).all()
             assert st["n_clusters"] == 1
+
+
+# Largest max |v|^2 for which the FP16 count folds the column norm into the
+# MMA: its accumulator G - ceil(|v_q|^2 / 2) is exact while
+# 3 max|v|^2 + 1 <= 2^25 (every partial sum then stays within 2^24).
+FOLD_LIMIT = ((1 << 25) - 1) // 3
+
+
+def fold_edge_points(seed: int, n: int, d: int, over: bool) -> np.ndarray:
+    """Rows whose largest |v|^2 sits just below (over=False) or just above
+    (over=True) the folded count's limit: 42 coordinates at the grid's ends
+    (v = -512 or 511) and one at +-418 (or +-419), so that G reaches about
+    +-1.1e7 between aligned and opposite rows; sign flips of shared base rows
+    put pair distances at every multiple of about 1023^2 below 2^24; copies
+    with one coordinate moved by one unit give distances next to those; the
+    other rows lie near the centre.  |v|^2 takes both parities."""
+    rng = np.random.default_rng(seed)
+    k, last = 42, (419 if over else 418)
+    v = rng.integers(-40, 41, size=(n, d))
+    m = (3 * n) // 4
+    base = rng.choice([-512, 511], size=(64, k))
+    rows = base[rng.integers(0, 64, size=m)].copy()
+    for i in range(m):
+        j = rng.integers(0, 16)
+        c = rng.choice(k, size=j, replace=False)
+        rows[i, c] = np.where(rows[i, c] == -512, 511, -512)
+    v[:m] = 0
+    v[:m, :k] = rows
+    v[:m, k] = rng.choice([-last, last], size=m)
+    v[0, :k] = -512  # the largest norm of the set
+    near = rng.integers(1, m, size=m // 4)
+    col = rng.integers(0, k + 1, size=near.size)
+    v[near, col] -= np.sign(v[near, col])
+    beta = (v.astype(np.int64) ** 2).sum(1)
+    assert (beta.max() > FOLD_LIMIT) == over and (beta & 1).any() and not (beta & 1).all()
+    u = v[rng.permutation(n)] + 512
+    return u.astype(np.float32) / np.float32(1024)
+
+
+@pytest.mark.parametrize("over", [False, True])
+def test_folded_count_at_its_norm_limit(over):
+    """The FP16 count runs its folded form up to the norm limit and falls back
+    to G alone above it; both give the oracle's exact counts, cores and labels."""
+    from paper_1506_02226_gb300.api import Plan
+    n, d = 4099, 64
+    x = fold_edge_points(2000 + int(over), n, d, over)
+    u = np.rint(x.astype(np.float64) * 1024).astype(np.int64)
+    rng = np.random.default_rng(5 + int(over))
+    for eps in thresholds_for(u, rng):
+        T = threshold(eps)
+        for min_pts in (2, 40):
+            want_lab, want_cnt, want_core = oracle.dbscan(x, eps, min_pts)
+            with Plan(max_n=n, max_d=d, grid=B.DBSCAN_GRID_OFF, precision=B.DBSCAN_PREC_FP16_GRAM) as p:
+                lab, cnt, core, st = p.run_detail(torch.from_numpy(x).cuda(), eps, min_pts)
+                folded = p.counters()[15]
+            assert st["path"] == B.DBSCAN_PATH_ALLPAIRS_TC
+            assert folded == (0 if over else 1), (T, folded)
+            np.testing.assert_array_equal(cnt.cpu().numpy(), want_cnt, err_msg=f"T={T} over={over}")
+            np.testing.assert_array_equal(core.cpu().numpy().astype(bool), want_core)
+            np.testing.assert_array_equal(lab.cpu().numpy(), want_lab, err_msg=f"T={T} mp={min_pts} over={over}")
