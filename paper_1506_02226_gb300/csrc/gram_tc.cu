@@ -347,15 +347,16 @@ __device__ __noinline__ int exact_sqdist(const int16_t *__restrict__ v16, int K,
 // again once its MMAs have completed; the epilogue holds only the tile's
 // metadata, in a ring of its own, so the operand ring runs up to NS tiles
 // ahead of the MMAs whatever the epilogue's pace.
-template <int KC, int NS, int NM, int RTN, int CR>
+template <int KC, int NS, int NM, int RTN, int CR, int NA = 2>
 struct __align__(16) SmemT {
     static constexpr int NSTAGE = NS;
     static constexpr int NMETA = NM;
-    uint16_t A[2 * RTN][TM * KC];    // two buffers of RTN row tiles (16 KB each for FP16, 32 KB for BF16)
+    static constexpr int NABUF = NA;
+    uint16_t A[NA * RTN][TM * KC];   // NA buffers of RTN row tiles (16 KB each for FP16, 32 KB for BF16)
     uint16_t B[NS][TN * KC];
-    MetaBlock metaA[2 * RTN];        // 2 KB per row tile
+    MetaBlock metaA[NA * RTN];       // 2 KB per row tile
     MetaBlock metaB[NM][2];          // NM x 4 KB
-    uint64_t a_full[2], a_empty[2];
+    uint64_t a_full[NA], a_empty[NA];
     uint64_t b_full[NS], b_empty[NS];
     uint64_t m_empty[NM];            // metadata stage released by the epilogue warps of its tile
     uint64_t t_full[2], t_empty[2];
@@ -373,12 +374,25 @@ struct __align__(16) SmemT {
 // stored columns (the folded chunk, below), 3 B stages of 40 KB and 4 metadata
 // stages; FP16 border: two row tiles, 4 and 5; FP16 merge and verification 5
 // and 6; BF16 2 and 6.
+#ifndef DB_TC_COUNT_CHUNK
+#define DB_TC_COUNT_CHUNK 32  // column tiles per work item of the count pass
+#endif
+#ifndef DB_TC_C16_NA
+#define DB_TC_C16_NA 2
+#endif
+#ifndef DB_TC_C16_NS
+#define DB_TC_C16_NS 3
+#endif
+#ifndef DB_TC_C16_NM
+#define DB_TC_C16_NM 4
+#endif
 template <int PASS, bool BF16>
 struct TcSmem {
     static constexpr bool RT2 = !BF16 && (PASS == TC_COUNT || PASS == TC_BORDER);
     static constexpr bool C16 = !BF16 && PASS == TC_COUNT;
-    using type = SmemT<BF16 ? 128 : (C16 ? 80 : 64), BF16 ? 2 : (C16 ? 3 : (RT2 ? 4 : 5)),
-                       C16 ? 4 : (RT2 ? 5 : 6), RT2 ? 2 : 1, PASS == TC_UNION ? 512 : 1>;
+    using type = SmemT<BF16 ? 128 : (C16 ? 80 : 64), BF16 ? 2 : (C16 ? DB_TC_C16_NS : (RT2 ? 4 : 5)),
+                       C16 ? DB_TC_C16_NM : (RT2 ? 5 : 6), RT2 ? 2 : 1, PASS == TC_UNION ? 512 : 1,
+                       C16 ? DB_TC_C16_NA : 2>;
 };
 
 // Work item w covers row unit rt (TMU rows: one 128-row tile, or two for the
@@ -443,7 +457,7 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
     // so the compiler keeps shared-space loads, stores and atomics.
     const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
     using Smem = typename TcSmem<PASS, BF16>::type;
-    constexpr int NSTAGE = Smem::NSTAGE, NMETA = Smem::NMETA;
+    constexpr int NSTAGE = Smem::NSTAGE, NMETA = Smem::NMETA, NA = Smem::NABUF;
     Smem &S = *reinterpret_cast<Smem *>(smem_raw + pad);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nR = *a.nR_ptr, nC = *a.nC_ptr;
@@ -454,9 +468,11 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
 
     volatile int *abort_flag = &S.abort_flag;
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < NA; ++i) {
             mbar_init(&S.a_full[i], 1);
             mbar_init(&S.a_empty[i], 1 + EPI_WARPS);
+        }
+        for (int i = 0; i < 2; ++i) {
             mbar_init(&S.t_full[i], 1);
             mbar_init(&S.t_empty[i], TILE_WARPS);
         }
@@ -499,18 +515,19 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
         // ---------------- producer ----------------
         if (lane == 0) {
             int t = 0, ia = 0;
-            int last_b[NSTAGE], last_a[2] = {-1, -1};  // phase of each buffer's last copy (-1: none)
+            int last_b[NSTAGE], last_a[NA];  // phase of each buffer's last copy (-1: none)
+            for (int i = 0; i < NA; ++i) last_a[i] = -1;
             for (int s = 0; s < NSTAGE; ++s) last_b[s] = -1;
             for (int w = blockIdx.x; w < nitems && !*abort_flag; w += gridDim.x, ++ia) {
                 int rt, c0, c1;
                 item_range<TMU>(a, w, nR, nC, rt, c0, c1);
-                const int ab = ia & 1;
-                if (!mbar_wait(&S.a_empty[ab], ((ia >> 1) & 1) ^ 1, abort_flag, a.wait_ns)) break;
+                const int ab = ia % NA;
+                if (!mbar_wait(&S.a_empty[ab], ((ia / NA) & 1) ^ 1, abort_flag, a.wait_ns)) break;
                 // RTN consecutive row tiles (the packed list holds whole 256-row tiles)
                 mbar_arrive_expect_tx(&S.a_full[ab], RTN * (a_bytes + (uint32_t)sizeof(MetaBlock)));
                 bulk_g2s(S.A[ab * RTN], a.opR + (size_t)rt * RTN * TM * KS, RTN * a_bytes, &S.a_full[ab]);
                 bulk_g2s(&S.metaA[ab * RTN], a.metaR + rt * RTN, RTN * (uint32_t)sizeof(MetaBlock), &S.a_full[ab]);
-                last_a[ab] = ia >> 1;
+                last_a[ab] = ia / NA;
                 for (int ct = c0; ct < c1; ++ct, ++t) {
                     const int s = t % NSTAGE, m = t % NMETA;
                     if (!TC_WAIT(w_prod, mbar_wait(&S.b_empty[s], ((t / NSTAGE) & 1) ^ 1, abort_flag, a.wait_ns)) ||
@@ -531,7 +548,7 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
                 bool ok = true;
                 for (int s = 0; s < NSTAGE; ++s)
                     if (last_b[s] >= 0) ok &= mbar_wait_quiet(&S.b_full[s], last_b[s] & 1, kDrainNs);
-                for (int ab = 0; ab < 2; ++ab)
+                for (int ab = 0; ab < NA; ++ab)
                     if (last_a[ab] >= 0) ok &= mbar_wait_quiet(&S.a_full[ab], last_a[ab] & 1, kDrainNs);
                 if (!ok) S.drain_failed = 1;
             }
@@ -548,8 +565,8 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
             for (int w = blockIdx.x; w < nitems && !*abort_flag; w += gridDim.x, ++ia) {
                 int rt, c0, c1;
                 item_range<TMU>(a, w, nR, nC, rt, c0, c1);
-                const int ab = ia & 1;
-                if (!mbar_wait(&S.a_full[ab], (ia >> 1) & 1, abort_flag, a.wait_ns)) break;
+                const int ab = ia % NA;
+                if (!mbar_wait(&S.a_full[ab], (ia / NA) & 1, abort_flag, a.wait_ns)) break;
                 bool ok = true;
                 for (int ct = c0; ct < c1 && ok; ++ct, ++t) {
                     const int s = t % NSTAGE;
@@ -602,15 +619,15 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
             }
             // Wait for the arrivals of the last commits, so that none lands after
             // the CTA has exited.  Stage s was last used by tile t_s (its phase
-            // t_s / NSTAGE); A buffer ab by item ia_ab (phase ia_ab / 2).
+            // t_s / NSTAGE); A buffer ab by item ia_ab (phase ia_ab / NA).
             if (clean && !*abort_flag) {
                 for (int s = 0; s < NSTAGE && s < t; ++s) {
                     const int ts = s + ((t - 1 - s) / NSTAGE) * NSTAGE;
                     mbar_wait(&S.b_empty[s], (ts / NSTAGE) & 1, abort_flag, a.wait_ns);
                 }
-                for (int ab = 0; ab < 2 && ab < ia; ++ab) {
-                    const int il = ab + ((ia - 1 - ab) / 2) * 2;
-                    mbar_wait(&S.a_empty[ab], (il >> 1) & 1, abort_flag, a.wait_ns);
+                for (int ab = 0; ab < NA && ab < ia; ++ab) {
+                    const int il = ab + ((ia - 1 - ab) / NA) * NA;
+                    mbar_wait(&S.a_empty[ab], (il / NA) & 1, abort_flag, a.wait_ns);
                 }
             }
             if (a.pass != TC_VERIFY && evaluated) atomicAdd(a.ctr + DB_CTR_EVAL + a.pass, evaluated);
@@ -637,10 +654,10 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
         for (int w = blockIdx.x; w < nitems; w += gridDim.x, ++ia) {
             int rt, c0, c1;
             item_range<TMU>(a, w, nR, nC, rt, c0, c1);
-            const int ab = ia & 1;
+            const int ab = ia % NA;
             // the row tile of the item this warp serves (its group's, with two)
             const int rsel = RTN == 2 ? ew / TILE_WARPS : 0;
-            if (!__all_sync(0xffffffffu, mbar_wait(&S.a_full[ab], (ia >> 1) & 1, abort_flag, a.wait_ns))) break;
+            if (!__all_sync(0xffffffffu, mbar_wait(&S.a_full[ab], (ia / NA) & 1, abort_flag, a.wait_ns))) break;
             const MetaBlock &ma = S.metaA[ab * RTN + rsel];
             const float beta_p = ma.beta[r], rho_p = ma.rho[r];
             const int p = ma.idx[r];
@@ -1202,7 +1219,7 @@ cudaError_t launch_allpairs_tc(const DbWork &w, const float *x, int64_t n64, int
     a.border = w.border;
     a.status = w.status;
     a.ctr = w.ctr;
-    a.col_chunk = 32;
+    a.col_chunk = DB_TC_COUNT_CHUNK;
     a.wait_ns = 2000000000ull;  // about two seconds per barrier wait
     // pass 1: all x all -> neighbour counts (the stall hook: a 50 ms budget the
     // waits exhaust, since no MMA completes)
@@ -1222,6 +1239,7 @@ cudaError_t launch_allpairs_tc(const DbWork &w, const float *x, int64_t n64, int
     a.pass = TC_COUNT;
     a.upper = 0;
     if ((e = launch_pass<TC_COUNT>(a, sms, st))) return e;
+    a.col_chunk = 32;
     w.marks->kernel("tc_count", st);
     a.ks = bf16 ? 2 * K : K;
     a.stall = 0;
