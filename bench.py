@@ -485,6 +485,10 @@ def run_ours(args, wl_name, baseline=True, steps=None):
                 ev_runs.append(pplan.pair_tests())
     if pplan.sync() != 0:
         raise RuntimeError("profiled run reported an error")
+    # FP16 tensor-core count: whether it ran the folded form (counter slot 15)
+    tc_form = None
+    if st0["path"] == B.DBSCAN_PATH_ALLPAIRS_TC and prec != B.DBSCAN_PREC_BF16_GRAM:
+        tc_form = "folded (column norm inside the MMA)" if pplan.counters()[15] else "G alone"
     pplan.close()
     total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
     if dist:
@@ -560,6 +564,7 @@ def run_ours(args, wl_name, baseline=True, steps=None):
                                      else n * n),
         "evaluated_vs_min": pairs_per_step / max(n * (n - 1) / 2, 1),
         "band_pairs_per_step": st0["band_pairs"],
+        "tc_count_form": tc_form,
         "points_per_s": world * n / (ms_per_step * 1e-3),
         "clusters": st0["n_clusters"], "core": st0["n_core"], "noise": st0["n_noise"],
         "kernels_ms": {k: round(v, 5) for k, v in sorted(avg.items(), key=lambda kv: -kv[1])},
@@ -877,7 +882,8 @@ def run_paper_compare(args, n=23_040, steps=3):
 def compact(rec: dict) -> dict:
     """The figures of a workload's record that the default line carries."""
     keep = ("metric", "value", "unit", "ms_per_step", "dtype", "pair_tests_per_step", "candidate_pairs_per_step",
-            "evaluated_vs_min", "band_pairs_per_step", "points_per_s", "launch_loop", "closed_loop", "poisson",
+            "evaluated_vs_min", "band_pairs_per_step", "tc_count_form", "points_per_s", "launch_loop", "closed_loop",
+            "poisson",
             "server_memory", "allpairs", "config", "clocks")
     out = {k: rec[k] for k in keep if k in rec}
     r = rec.get("roofline")
