@@ -342,12 +342,14 @@ def cpu_baseline(inst, wl_name, desc):
                               "sample": f"{m1}-point subsample ({m1 * m1} pair tests, {dt1:.2f} s)"}}
 
 
-def roofline(dom: str, avg_ms: float, ev: list, n: int, d: int, gs, wl_name: str, traffic):
+def roofline(dom: str, avg_ms: float, ev: list, n: int, d: int, gs, wl_name: str, traffic, folded: bool = False):
     """Roofline of the dominant kernel from its CUDA-event time and the pairs it evaluated.
 
     Pair kernels: the tensor-core passes against the measured bf16 peak (2K FLOPs
-    per pair, K = d padded to 16) with the epilogue's ~3 FP32 operations per pair
-    beside it; CUDA-core pair kernels (all-pairs tile and the eps-grid's count,
+    per pair, K = d padded to 16) with the epilogue's FP32 operations per pair
+    beside it (about 3; 1.5 for the folded FP16 count, whose MMA also runs one
+    more K chunk of 16: the MMA work it executes is reported beside the useful
+    work); CUDA-core pair kernels (all-pairs tile and the eps-grid's count,
     merge and border) against the FP32 pipe at d+2 (Gram form) or 2d+1 (direct
     form) operations per evaluated pair, with the eps-grid kernels' HBM
     fraction beside it.  Other kernels against HBM."""
@@ -364,9 +366,15 @@ def roofline(dom: str, avg_ms: float, ev: list, n: int, d: int, gs, wl_name: str
                     "peak_src": peaks["src"] + " bf16 burst (FP16 dense rate is the same)",
                     "algorithmic_flops": flops, "pairs": pairs, "avg_ms": avg_ms}
             fp32_peak, _ = fp32_peak_tops()
-            alu = 3.0 * pairs / sec / 1e12
-            roof["epilogue_fp32"] = {"ops_per_pair": 3, "achieved": alu, "peak": fp32_peak, "unit": "T ops/s",
+            opp = 1.5 if (folded and dom == "tc_count") else 3
+            alu = opp * pairs / sec / 1e12
+            roof["epilogue_fp32"] = {"ops_per_pair": opp, "achieved": alu, "peak": fp32_peak, "unit": "T ops/s",
                                      "frac": alu / fp32_peak}
+            if folded and dom == "tc_count":
+                ex = 2.0 * pairs * (K + 16) / sec / 1e12
+                roof["mma_executed"] = {"flops_per_pair": 2 * (K + 16), "achieved": ex, "unit": "TFLOP/s",
+                                        "frac": ex / peaks["bf16_tflops"],
+                                        "note": "the folded count's MMA runs K + 16 columns; frac above counts 2K"}
             return roof
         ops_pp = pair_ops(d) if not dom.startswith(("grid_", "mid_")) else d + 2
         fp32_peak, sms = fp32_peak_tops()
@@ -539,11 +547,12 @@ def run_ours(args, wl_name, baseline=True, steps=None):
     avg = {k: statistics.mean(v) for k, v in kern.items()}
     ev_pass = [statistics.mean(r[k] for r in ev_runs) for k in range(4)]
     dom = max(avg, key=avg.get)
-    roof = roofline(dom, avg[dom], ev_pass, n, d, gs, wl_name, args.traffic)
+    folded = tc_form is not None and tc_form.startswith("folded")
+    roof = roofline(dom, avg[dom], ev_pass, n, d, gs, wl_name, args.traffic, folded)
     others = {}
     for k in sorted(avg, key=avg.get, reverse=True)[1:4]:
         if k in PASS_OF and ev_pass[PASS_OF[k]] > 0:
-            r = roofline(k, avg[k], ev_pass, n, d, gs, wl_name, None)
+            r = roofline(k, avg[k], ev_pass, n, d, gs, wl_name, None, folded)
             others[k] = {"bound": r["bound"], "frac": r["frac"], "achieved": r["achieved"], "unit": r["unit"],
                          "pairs": r.get("pairs"), "avg_ms": avg[k]}
     cpu = cpu_baseline(inst, wl_name, desc) if (baseline and not args.no_baseline) else None
@@ -889,7 +898,7 @@ def compact(rec: dict) -> dict:
     r = rec.get("roofline")
     if r:
         out["roofline"] = {k: r[k] for k in ("kernel", "bound", "achieved", "peak", "unit", "frac", "avg_ms",
-                                             "epilogue_fp32", "other_bound") if k in r}
+                                             "epilogue_fp32", "mma_executed", "other_bound") if k in r}
     if rec.get("e2e"):
         out["e2e"] = {k: rec["e2e"][k] for k in ("value", "unit", "ms_per_step") if k in rec["e2e"]}
     if rec.get("cpu_baseline"):
