@@ -28,6 +28,21 @@
 //   rho_p rho_q covers the band).  The band holds only pairs within 16K
 //   squared units of the threshold.
 //
+// Folded FP16 count.  The count pass appends one 16-column chunk to each
+// operand row so that the MMA also subtracts the column term: rows carry
+// 1, 2^11, 2^15 and columns the negated digits of h_q = ceil(|v_q|^2 / 2)
+// (integers FP16 holds exactly), and the accumulator holds G - h_q.  Every
+// term of that sum is an integer and their magnitudes add up to at most
+// |v_p||v_q| + h_q <= (|v_p|^2 + 2|v_q|^2 + 1) / 2, so when
+// 3 max|v|^2 + 1 <= 2^25 every partial sum, in any order of accumulation, is
+// an integer of magnitude <= 2^24 and the accumulator is exact.  The columns
+// are ordered even |v_q|^2 first (odd ones from the next 256-column tile on),
+// so each tile has one parity f and each row one threshold per parity:
+// D <= T iff G - h_q >= ceil((|v_p|^2 - T - f) / 2).  The epilogue then needs
+// one saturating add per pair and no column data.  Inputs with larger norms
+// (only the extreme corners of the grid reach them at d = 64) run the same
+// pass on G alone with the column norms; the pass decides on the device.
+//
 // Data layout.  Each operand list (all points, core points, non-core points)
 // is packed once into 128-row tiles in the canonical K-major layout without
 // swizzle: 8 x 8 core matrices of 128 contiguous bytes, K-adjacent core
@@ -37,20 +52,27 @@
 // metadata {beta, rho, index} rides along in the same copy group.
 //
 // CTA roles (320 threads for the FP16 count and the verification, 576
-// otherwise; one CTA per SM, persistent over work items):
-//   warp 0      producer: bulk copies of A tiles (2 buffers), B tiles (a ring
-//               of 5 stages, 2 for BF16, each freed by the MMA commit of its
-//               tile) and their metadata (a 6-stage ring, freed by the
-//               epilogue), completion via mbarrier transaction counts
+// otherwise; one CTA per SM, persistent over work items of one row unit and
+// a chunk of column tiles):
+//   warp 0      producer: bulk copies of A tiles (2 buffers, each holding the
+//               item's row tiles: two for the FP16 count and border, one
+//               otherwise), B tiles (a ring of 3 stages for the FP16 count, 4
+//               for the FP16 border, 5 for the merge, 2 for BF16, each freed by
+//               the MMA commit of its tile) and their metadata (a ring of 4 to
+//               6 stages, freed by the epilogue), completion via mbarrier
+//               transaction counts
 //   warp 1      TMEM owner (alloc/dealloc of 512 columns) and MMA issuer:
-//               K/16 tcgen05.mma (M=128, N=256, K=16) per tile into one of two
-//               256-column accumulators; tcgen05.commit signals the epilogue
+//               K/16 tcgen05.mma (M=128, N=256, K=16) per MMA tile into one of
+//               two 256-column accumulators (with two row tiles, each B tile
+//               feeds one MMA tile per row tile, one per accumulator);
+//               tcgen05.commit signals the epilogue
 //   warps 2..   epilogue: tcgen05.ld of the accumulator (one TMEM lane = one
-//               row; in the FP16 count one warp per lane quadrant and tile,
-//               the two accumulator buffers served by two groups; otherwise
-//               two or four warps per lane quadrant split the 256 columns), the
-//               exact decision above, and the pass's consumer: neighbour count,
-//               union of core-core neighbours, or smallest core neighbour.
+//               row; with two row tiles a group of warps per row tile and
+//               accumulator, in the FP16 count one warp per lane quadrant,
+//               otherwise two or four warps per lane quadrant split the 256
+//               columns), the exact decision above, and the pass's consumer:
+//               neighbour count, union of core-core neighbours, or smallest
+//               core neighbour.
 // Every wait is bounded (about two seconds of %globaltimer); on expiry the CTA
 // records DB_EBIT_TIMEOUT, stops issuing work, waits for its own copies and
 // MMAs, frees its TMEM and returns.
