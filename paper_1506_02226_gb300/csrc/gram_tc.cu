@@ -713,14 +713,15 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
                 const MetaBlock &mc = S.metaB[m][half];
                 int *colroot = S.colroot + (PASS == TC_UNION ? (b * 2 + half) * 128 : 0);
                 bool hints = false;  // union: colroot filled for this tile
-                // union: the parents of this tile's 128 column points, loaded now so
-                // that their latency hides behind the accumulator loads and scores
-                int pr[4] = {-1, -1, -1, -1};
+                // union: the parents of this warp's GW * NG column points of the
+                // tile, loaded now so that their latency hides behind the
+                // accumulator loads and scores
+                int pr[NG];
                 if (PASS == TC_UNION) {
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const int q = mc.idx[lane + 32 * k];
-                        if (q >= 0) pr[k] = db::ld_relaxed(a.parent + q);
+                    for (int k = 0; k < NG; ++k) {
+                        const int q = mc.idx[moff + lane + GW * k];
+                        pr[k] = q >= 0 ? db::ld_relaxed(a.parent + q) : -1;
                     }
                 }
                 if constexpr (PASS == TC_COUNT && !BF16) {
@@ -865,11 +866,11 @@ __global__ void __launch_bounds__(tc_threads<PASS, BF16>(), 1) tc_pass_kernel(Tc
                     const bool need = row_ok && mx >= thr && (PASS != TC_BORDER || mc.idx[cb] < bmin);
                     if (!__any_sync(0xffffffffu, need)) continue;
                     if (PASS == TC_UNION && !hints) {
-                        // the parents loaded at the tile's start (the four warps of the
-                        // half all write them: any value is a member of the column
-                        // point's set)
+                        // the parents loaded at the tile's start, for this warp's columns
+                        // (the warps of the other lane quadrants that share them write
+                        // them too: any value is a member of the column point's set)
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) colroot[lane + 32 * k] = pr[k];
+                        for (int k = 0; k < NG; ++k) colroot[moff + lane + GW * k] = pr[k];
                         __syncwarp();
                         hints = true;
                     }
