@@ -396,8 +396,11 @@ struct __align__(16) SmemT {
 // stored columns (the folded chunk, below), 3 B stages of 40 KB and 4 metadata
 // stages; FP16 border: two row tiles, 4 and 5; FP16 merge and verification 5
 // and 6; BF16 2 and 6.
+// Compile-time knobs of the FP16 count (the defaults measured best or within
+// noise of the alternatives): column tiles per work item, A buffers, B stages
+// and metadata stages.
 #ifndef DB_TC_COUNT_CHUNK
-#define DB_TC_COUNT_CHUNK 32  // column tiles per work item of the count pass
+#define DB_TC_COUNT_CHUNK 32
 #endif
 #ifndef DB_TC_C16_NA
 #define DB_TC_C16_NA 2
@@ -418,7 +421,7 @@ struct TcSmem {
 };
 
 // Work item w covers row unit rt (TMU rows: one 128-row tile, or two for the
-// FP16 count) and column tiles [c0, c1) of one column chunk.
+// FP16 count and border) and column tiles [c0, c1) of one column chunk.
 // Count and border passes: ch = w / nrt, rt = w % nrt, so the CTAs running at
 // one time share their column chunk and its B tiles come from L2.  Merge pass
 // (a.upper): rt = w / nchunk and the chunk rotates with the row tile, so the
