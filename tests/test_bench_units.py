@@ -64,3 +64,33 @@ def test_candidate_pairs_bound_the_neighbour_pairs():
     nbr = (diff ** 2).sum(-1) <= T
     gs = bench.grid_structure(x, eps)
     assert gs["candidate_pairs"] >= int(nbr.sum())
+
+
+def test_tensor_core_roofline_arithmetic(monkeypatch):
+    """The tensor-core roofline: 2K useful FLOPs per evaluated pair against the
+    measured bf16 peak, the epilogue's FP32 operations beside it (3 per pair,
+    1.5 for the folded count), and for the folded count the MMA work it
+    executes (2 (K + 16) FLOPs per pair) beside the useful work.  (The FP32
+    peak needs the GPU's SM count; here it is the GB300's 152 SMs.)"""
+    monkeypatch.setattr(bench, "fp32_peak_tops", lambda: (152 * 128 * 2.07e9 / 1e12, 152))
+    peaks = bench.load_peaks()
+    pairs = [4 * 10 ** 10, 7 * 10 ** 9, 10 ** 10, 0]
+    ms = 5.0
+    for folded in (False, True):
+        r = bench.roofline("tc_count", ms, pairs, 200_000, 64, None, "highd", None, folded)
+        assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+        assert math.isclose(r["achieved"], 2 * 64 * pairs[0] / (ms * 1e-3) / 1e12)
+        assert math.isclose(r["frac"], r["achieved"] / peaks["bf16_tflops"])
+        assert r["epilogue_fp32"]["ops_per_pair"] == (1.5 if folded else 3)
+        if folded:
+            ex = r["mma_executed"]
+            assert ex["flops_per_pair"] == 2 * (64 + 16)
+            assert math.isclose(ex["achieved"], r["achieved"] * 80 / 64)
+        else:
+            assert "mma_executed" not in r
+    # other passes keep 3 operations per pair and report no executed MMA rate, folded or not
+    r = bench.roofline("tc_union", ms, pairs, 200_000, 64, None, "highd", None, True)
+    assert r["epilogue_fp32"]["ops_per_pair"] == 3 and "mma_executed" not in r
+    # d = 48 pads to K = 48
+    r = bench.roofline("tc_border", ms, pairs, 200_000, 48, None, "highd", None, False)
+    assert math.isclose(r["achieved"], 2 * 48 * pairs[2] / (ms * 1e-3) / 1e12)
