@@ -80,6 +80,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cmath>
 
@@ -1183,12 +1184,17 @@ size_t tc_smem_bytes() {
 
 template <int PASS, bool BF16>
 cudaError_t launch_pass_t(const TcArgs &a, int sms, cudaStream_t st) {
-    static bool attr = false;  // one process-wide attribute per instantiation
-    if (!attr) {
+    // the shared-memory attribute, set once per device (plans may live on
+    // several devices of one process; setting it twice is harmless)
+    static std::atomic<unsigned long long> attr_set{0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+    if (!(attr_set.load(std::memory_order_relaxed) & bit) || !bit) {
         cudaError_t e = cudaFuncSetAttribute(tc_pass_kernel<PASS, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)tc_smem_bytes<PASS, BF16>());
         if (e) return e;
-        attr = true;
+        attr_set.fetch_or(bit, std::memory_order_relaxed);
     }
     tc_pass_kernel<PASS, BF16><<<sms, tc_threads<PASS, BF16>(), tc_smem_bytes<PASS, BF16>(), st>>>(a);
     return cudaGetLastError();
